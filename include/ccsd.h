@@ -1,0 +1,149 @@
+/*
+ * ccsd.h -- C ABI of the GB300 library for biorthonormal CCSD derivative
+ * couplings (Kjonstad & Koch, "Non-adiabatic derivative coupling elements for
+ * the coupled cluster singles and doubles model").
+ *
+ * Problem statement (Theory section): a closed-shell Hamiltonian with
+ * one-electron integrals h_pq and two-electron integrals in Cholesky form
+ * g_pqrs = sum_J B^J_pq B^J_rs; the CCSD ground state, EOM-CCSD left/right
+ * states, and the biorthonormal derivative coupling F_kl = <psi_k^L | d/dx psi_l^R>
+ * (Eq. nac) along a perturbation x of (h, B), evaluated with the Lagrangian of
+ * the Lagrangian section (Eqs. for gamma, t-eta, amplituderelax, NAC_NC).
+ *
+ * Conventions shared by all calls
+ * - Orbitals: n = o + v, occupied first.  Arrays are FP64, row-major (C order).
+ * - eps[n]: orbital energies; used only for the denominators of the
+ *   preconditioners (D_ai = eps_a - eps_i, D_aibj = eps_a + eps_b - eps_i - eps_j).
+ * - h[n*n] symmetric; B[naux*n*n] with B^J symmetric in pq.
+ * - Amplitude-like vectors have dim = o*v + o*o*v*v entries: singles x[i][a]
+ *   followed by doubles x[i][j][a][b] with x_ijab = x_jiba.  The doubles entry is
+ *   the packed coefficient of the excitation tau_aibj (ai >= bj) of the
+ *   biorthonormal basis, stored at both (i,j,a,b) and (j,i,b,a); inner products
+ *   are the packed ones, sum_ai x_ai y_ai + sum_{ai >= bj} x_aibj y_aibj.
+ * - Pointers: every array argument may be host or device memory; the library
+ *   detects which (cudaPointerGetAttributes) and writes outputs to the same
+ *   memory space as given.  The caller owns all buffers it passes.
+ * - Streams: all GPU work runs on options.stream (0 = the legacy default
+ *   stream).  Calls that return host values synchronise that stream.
+ * - Errors: every call returns a ccsd_status; no C++ exception crosses the
+ *   ABI.  ccsd_last_error(handle) gives the message of the last failure.
+ * - Threads: a handle must not be used by two threads at once.
+ * - State indices: k, l in {0 = ground state, 1..nroots}; the excited states
+ *   are those of the last eom_solve_right/left pair.  For k = 0 the left
+ *   ground state is <HF|(1 + Lambda) exp(-T).
+ */
+#ifndef CCSD_GB300_H
+#define CCSD_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ccsd_ctx* ccsd_handle;
+
+typedef enum {
+  CCSD_OK = 0,
+  CCSD_ERR_ARG = 1,           /* invalid argument (sizes, NULL, asymmetric B, bad state index) */
+  CCSD_ERR_OOM = 2,           /* device allocation failed */
+  CCSD_ERR_CUDA = 3,          /* CUDA runtime error */
+  CCSD_ERR_STATE = 4,         /* call made before its prerequisites (e.g. EOM before ground) */
+  CCSD_ERR_NOT_CONVERGED = 5, /* iteration limit reached */
+  CCSD_ERR_COMPLEX_ROOT = 6,  /* a wanted EOM root came out complex (defective intersection) */
+  CCSD_ERR_DEGENERATE = 7,    /* omega_l - omega_k below the degeneracy threshold */
+  CCSD_ERR_NOT_HF = 8,        /* reserved: relaxed-orbital mode needs an HF reference */
+  CCSD_ERR_TIMEOUT = 9        /* a device-side wait exceeded its budget */
+} ccsd_status;
+
+enum { CCSD_PREC_FP64 = 0, CCSD_PREC_MIXED = 1 };
+enum { CCSD_GUESS_MP2 = 0 };
+
+typedef struct {
+  int precision;        /* CCSD_PREC_FP64 or CCSD_PREC_MIXED (tensor-core split products) */
+  int splits;           /* mixed mode: bf16 slices per FP64 operand (2 or 3) */
+  int relax_orbitals;   /* must be 0: orbitals are fixed and x-independent */
+  double tol_res;       /* ground state: max |Omega| */
+  double tol_eom;       /* EOM: packed residual norm */
+  double tol_lin;       /* Lambda and zeta equations: max |residual| */
+  double tol_degen;     /* |omega_l - omega_k| below this -> CCSD_ERR_DEGENERATE */
+  int max_iter;         /* per solver */
+  int diis_dim;         /* DIIS history length */
+  int davidson_block;   /* trial vectors transformed per block (<= 16) */
+  int davidson_max_sub; /* subspace size before restart */
+  int guess;            /* CCSD_GUESS_MP2 */
+  void* stream;         /* cudaStream_t, 0 = default */
+} ccsd_options;
+
+/* Fill *opt with defaults (FP64, tol_res 1e-10, tol_eom 1e-7, tol_lin 1e-9, ...). */
+void ccsd_default_options(ccsd_options* opt);
+
+/* Create a handle for the Hamiltonian (eps, h, B) with o occupied and v virtual
+ * orbitals and naux Cholesky vectors.  Copies the inputs to the device, checks
+ * that h and every B^J are symmetric (1e-10, else CCSD_ERR_ARG) and builds the
+ * Hamiltonian-only intermediates (the bare vvvv, ovvv and ovov integral blocks).
+ * opt may be NULL (defaults).  On failure *out is NULL. */
+ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int o, int v, int naux,
+                        const ccsd_options* opt, ccsd_handle* out);
+
+/* Solve Omega(t) = 0 (Theory section, amplitude equations) by DIIS-accelerated
+ * Jacobi iterations from the MP2-like guess t = -Omega(0)/D.  Also solves the
+ * ground-state multipliers lambda^T A = -eta^T.  Returns E_CCSD (total
+ * electronic energy <HF|Hbar|HF>) and the iteration count (either may be NULL). */
+ccsd_status ccsd_solve_ground(ccsd_handle h, double* e_ccsd, int* iters);
+
+/* Lowest nroots roots (by real part) of A R = omega R (right) with block
+ * Davidson; omega[nroots] output (may be NULL).  R_k is normalised to unit
+ * packed norm with its largest-magnitude component positive, and
+ * R_0^k = eta^T R_k / omega_k. */
+ccsd_status eom_solve_right(ccsd_handle h, int nroots, double* omega, int* iters);
+/* Left states L_k^T A = omega_k L_k^T for the same nroots; afterwards the left
+ * states are biorthonormalised against the right ones, L_k^T R_l = delta_kl
+ * (Eq. for the states, L_0^k = 0).  Requires eom_solve_right first. */
+ccsd_status eom_solve_left(ccsd_handle h, int nroots, double* omega, int* iters);
+
+/* One block Jacobian transformation at the converged amplitudes:
+ * side 0: y_i = A x_i; side 1: y_i = (x_i^T A)^T (Eq. for A), for i < nvec.
+ * x, y: [nvec][dim] (host or device). */
+ccsd_status ccsd_jacobian_transform(ccsd_handle h, int side, int nvec, const double* x, double* y);
+
+/* Residual Omega(t) and energy at amplitudes t[dim] (no convergence implied).
+ * omega[dim] output; e may be NULL. */
+ccsd_status ccsd_residual(ccsd_handle h, const double* t, double* omega, double* e);
+
+/* Copy out the converged amplitudes t[dim], the ground multipliers lambda[dim],
+ * and EOM states right[k][dim] / left[k][dim] (NULL pointers are skipped). */
+ccsd_status ccsd_get_amplitudes(ccsd_handle h, double* t, double* lambda);
+ccsd_status ccsd_get_states(ccsd_handle h, int nroots, double* r0, double* right, double* left);
+
+/* Coupling densities for the pair (k, l), k != l: the gradient with respect
+ * to (h, B) of the Lagrangian's Hamiltonian-dependent part, so that
+ * F_kl^x = sum_pq D_pq dh_pq + sum_Jpq Z_Jpq dB_Jpq (Eq. NAC_NC; the orbital
+ * term vanishes because the orbitals are fixed).  D[n*n], Z[naux*n*n] outputs
+ * (Z may be NULL).  Solves the zeta equations of Eq. amplituderelax (or uses
+ * the closed form for l = 0). */
+ccsd_status ccsd_coupling_densities(ccsd_handle h, int k, int l, double* D, double* Z);
+
+/* F[d] = F_kl^x along ndir directions: dh[d][n*n], dB[d][naux*n*n]. */
+ccsd_status ccsd_derivative_coupling(ccsd_handle h, int k, int l, int ndir, const double* dh, const double* dB,
+                                     double* F);
+
+/* Seconds spent in the last call and counters of the executor (GEMM calls,
+ * tensor-core calls and their flops) since creation; any pointer may be NULL. */
+ccsd_status ccsd_stats(ccsd_handle h, double* flops_fp64, double* flops_tc, long long* gemms, long long* tc_gemms);
+
+const char* ccsd_strerror(ccsd_status s);
+const char* ccsd_last_error(ccsd_handle h);
+void ccsd_destroy(ccsd_handle h);
+
+/* Host-only: text description of one of the library's tensor programs
+ * ("fwd", "jvp", "vjp", "hvp", "dens1", "dens0").  Writes at most len bytes
+ * (NUL-terminated) and returns the full length needed (without the NUL), or
+ * -1 for an unknown name.  Touches no GPU. */
+long long ccsd_describe_program(const char* which, char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCSD_GB300_H */

@@ -354,14 +354,16 @@ class System:
             if np.abs(omega - omega_l).max() > 1e-6:
                 raise RuntimeError("left and right EOM roots differ")
         R = [self.normalize_right(r) for r in R]
-        # biorthonormalise: L_k^T R_l = delta_kl (roots are non-degenerate)
+        # biorthonormalise: L_k^T R_l = delta_kl (roots are non-degenerate).
+        # With M[m, l] = <L_m|R_l> and L'_k = sum_m c[m, k] L_m, <L'_k|R_l> = (c^T M)[k, l],
+        # so c = M^{-T}.
         M = np.array([[L[k].dot(R[l]) for l in range(nroots)] for k in range(nroots)])
-        Minv = np.linalg.inv(M)
+        c = np.linalg.inv(M).T
         Lnew = []
         for k in range(nroots):
-            x = L[0] * Minv[0, k]
+            x = L[0] * c[0, k]
             for m in range(1, nroots):
-                x = x + L[m] * Minv[m, k]
+                x = x + L[m] * c[m, k]
             Lnew.append(x)
         eta = self.eta(t)
         right = [State(eta.dot(R[k]) / omega[k], R[k]) for k in range(nroots)]

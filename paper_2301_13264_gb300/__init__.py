@@ -1,0 +1,24 @@
+"""GB300 library for biorthonormal CCSD non-adiabatic derivative couplings.
+
+The computation lives in the CUDA library libccsd_gb300.so (C ABI declared in
+include/ccsd.h); :mod:`.binding` loads it with ctypes.  :mod:`.synth` draws
+seeded synthetic Hamiltonians.
+"""
+from .binding import (  # noqa: F401
+    CCSDError,
+    ccsd_coupling_densities,
+    ccsd_create,
+    ccsd_default_options,
+    ccsd_derivative_coupling,
+    ccsd_describe_program,
+    ccsd_destroy,
+    ccsd_get_amplitudes,
+    ccsd_get_states,
+    ccsd_jacobian_transform,
+    ccsd_residual,
+    ccsd_solve_ground,
+    ccsd_stats,
+    eom_solve_left,
+    eom_solve_right,
+    vector_dim,
+)

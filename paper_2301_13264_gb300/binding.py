@@ -1,0 +1,200 @@
+"""ctypes binding of libccsd_gb300.so (see include/ccsd.h).
+
+Argument marshalling only: every function forwards to the C entry point of the
+same name.  Arrays may be numpy arrays (host memory) or torch tensors (host or
+CUDA memory); they must be contiguous float64.  The library raises no Python
+fallback: if it is not built, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libccsd_gb300.so")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_NOT_CONVERGED, ERR_COMPLEX_ROOT, ERR_DEGENERATE, ERR_NOT_HF, \
+    ERR_TIMEOUT = range(10)
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("splits", ctypes.c_int),
+        ("relax_orbitals", ctypes.c_int),
+        ("tol_res", ctypes.c_double),
+        ("tol_eom", ctypes.c_double),
+        ("tol_lin", ctypes.c_double),
+        ("tol_degen", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("diis_dim", ctypes.c_int),
+        ("davidson_block", ctypes.c_int),
+        ("davidson_max_sub", ctypes.c_int),
+        ("guess", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class CCSDError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built ({LIB_PATH}); run paper_2301_13264_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.ccsd_default_options.argtypes = [ctypes.POINTER(Options)]
+        L.ccsd_default_options.restype = None
+        L.ccsd_create.argtypes = [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Options),
+                                  ctypes.POINTER(_P)]
+        L.ccsd_solve_ground.argtypes = [_P, _D, ctypes.POINTER(ctypes.c_int)]
+        L.eom_solve_right.argtypes = [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int)]
+        L.eom_solve_left.argtypes = [_P, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int)]
+        L.ccsd_jacobian_transform.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
+        L.ccsd_residual.argtypes = [_P, _P, _P, _D]
+        L.ccsd_get_amplitudes.argtypes = [_P, _P, _P]
+        L.ccsd_get_states.argtypes = [_P, ctypes.c_int, _D, _P, _P]
+        L.ccsd_coupling_densities.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
+        L.ccsd_derivative_coupling.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _D]
+        L.ccsd_stats.argtypes = [_P, _D, _D, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+        L.ccsd_strerror.argtypes = [ctypes.c_int]
+        L.ccsd_strerror.restype = ctypes.c_char_p
+        L.ccsd_last_error.argtypes = [_P]
+        L.ccsd_last_error.restype = ctypes.c_char_p
+        L.ccsd_destroy.argtypes = [_P]
+        L.ccsd_destroy.restype = None
+        L.ccsd_describe_program.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_size_t]
+        L.ccsd_describe_program.restype = ctypes.c_longlong
+        for name in ("ccsd_create", "ccsd_solve_ground", "eom_solve_right", "eom_solve_left",
+                     "ccsd_jacobian_transform", "ccsd_residual", "ccsd_get_amplitudes", "ccsd_get_states",
+                     "ccsd_coupling_densities", "ccsd_derivative_coupling", "ccsd_stats"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Raw pointer of a contiguous float64 numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous float64")
+        return ctypes.c_void_p(x.ctypes.data)
+    # torch tensor
+    import torch
+    if x.dtype != torch.float64 or not x.is_contiguous():
+        raise ValueError("tensors must be contiguous float64")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _check(h, status):
+    if status != OK:
+        msg = lib().ccsd_last_error(h).decode() if h else lib().ccsd_strerror(status).decode()
+        raise CCSDError(status, msg)
+
+
+def ccsd_default_options(**kw) -> Options:
+    opt = Options()
+    lib().ccsd_default_options(ctypes.byref(opt))
+    for k, v in kw.items():
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = v.cuda_stream  # torch.cuda.Stream
+        setattr(opt, k, v)
+    return opt
+
+
+def ccsd_create(eps, h, B, o, v, naux, options: Options | None = None):
+    handle = _P()
+    st = lib().ccsd_create(_ptr(eps), _ptr(h), _ptr(B), o, v, naux,
+                           ctypes.byref(options) if options is not None else None, ctypes.byref(handle))
+    _check(None, st)
+    return handle
+
+
+def ccsd_solve_ground(h):
+    e = ctypes.c_double()
+    it = ctypes.c_int()
+    _check(h, lib().ccsd_solve_ground(h, ctypes.byref(e), ctypes.byref(it)))
+    return e.value, it.value
+
+
+def eom_solve_right(h, nroots):
+    w = (ctypes.c_double * nroots)()
+    it = ctypes.c_int()
+    _check(h, lib().eom_solve_right(h, nroots, w, ctypes.byref(it)))
+    return list(w), it.value
+
+
+def eom_solve_left(h, nroots):
+    w = (ctypes.c_double * nroots)()
+    it = ctypes.c_int()
+    _check(h, lib().eom_solve_left(h, nroots, w, ctypes.byref(it)))
+    return list(w), it.value
+
+
+def ccsd_jacobian_transform(h, side, nvec, x, y):
+    _check(h, lib().ccsd_jacobian_transform(h, side, nvec, _ptr(x), _ptr(y)))
+
+
+def ccsd_residual(h, t, omega):
+    e = ctypes.c_double()
+    _check(h, lib().ccsd_residual(h, _ptr(t), _ptr(omega), ctypes.byref(e)))
+    return e.value
+
+
+def ccsd_get_amplitudes(h, t=None, lam=None):
+    _check(h, lib().ccsd_get_amplitudes(h, _ptr(t), _ptr(lam)))
+
+
+def ccsd_get_states(h, nroots, right=None, left=None):
+    r0 = (ctypes.c_double * nroots)()
+    _check(h, lib().ccsd_get_states(h, nroots, r0, _ptr(right), _ptr(left)))
+    return list(r0)
+
+
+def ccsd_coupling_densities(h, k, l, D, Z=None):
+    _check(h, lib().ccsd_coupling_densities(h, k, l, _ptr(D), _ptr(Z)))
+
+
+def ccsd_derivative_coupling(h, k, l, ndir, dh, dB):
+    F = (ctypes.c_double * ndir)()
+    _check(h, lib().ccsd_derivative_coupling(h, k, l, ndir, _ptr(dh), _ptr(dB), F))
+    return list(F)
+
+
+def ccsd_stats(h):
+    f64, ftc = ctypes.c_double(), ctypes.c_double()
+    g, gt = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(h, lib().ccsd_stats(h, ctypes.byref(f64), ctypes.byref(ftc), ctypes.byref(g), ctypes.byref(gt)))
+    return {"flops_fp64": f64.value, "flops_tc": ftc.value, "gemms": g.value, "tc_gemms": gt.value}
+
+
+def ccsd_destroy(h):
+    if h:
+        lib().ccsd_destroy(h)
+
+
+def ccsd_describe_program(which: str) -> str:
+    n = lib().ccsd_describe_program(which.encode(), None, 0)
+    if n < 0:
+        raise ValueError(f"unknown program {which}")
+    buf = ctypes.create_string_buffer(n + 1)
+    lib().ccsd_describe_program(which.encode(), buf, n + 1)
+    return buf.value.decode()
+
+
+def vector_dim(o: int, v: int) -> int:
+    return o * v + o * o * v * v

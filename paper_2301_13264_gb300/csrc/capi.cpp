@@ -1,0 +1,883 @@
+// C ABI: handle, solvers (ground state, Lambda, EOM, coupling multipliers),
+// coupling densities and derivative couplings.  All vector arithmetic runs in
+// the library's CUDA kernels; the host only solves the small subspace problems.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/ccsd.h"
+#include "exec.h"
+#include "kernels.cuh"
+#include "programs.h"
+#include "small_linalg.h"
+
+using namespace ccsd;
+
+namespace {
+
+struct Err : std::runtime_error {
+  ccsd_status code;
+  Err(ccsd_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define CUDA_OK(x)                                                                                 \
+  do {                                                                                             \
+    cudaError_t e_ = (x);                                                                          \
+    if (e_ == cudaErrorMemoryAllocation) throw Err(CCSD_ERR_OOM, std::string(#x ": out of memory")); \
+    if (e_ != cudaSuccess) throw Err(CCSD_ERR_CUDA, std::string(#x ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct DevBuf {
+  double* p = nullptr;
+  int64_t n = 0;
+  DevBuf() = default;
+  explicit DevBuf(int64_t n_) { alloc(n_); }
+  void alloc(int64_t n_) {
+    release();
+    n = n_;
+    CUDA_OK(cudaMalloc(&p, std::max<int64_t>(n, 1) * sizeof(double)));
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  ~DevBuf() { release(); }
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+};
+
+}  // namespace
+
+struct ccsd_ctx {
+  ccsd_options opt;
+  int o = 0, v = 0, naux = 0, n = 0;
+  VecShape vs;
+  int64_t dim = 0, n1 = 0;
+  cudaStream_t st = 0;
+  Programs P;
+  std::unique_ptr<Executor> ex;
+  DevBuf eps, h, B, ones;
+  DevBuf t, lam, eta, omega_buf, escal, seedE, gsc;  // amplitudes, multipliers, scratch
+  std::vector<std::unique_ptr<DevBuf>> R, L;
+  std::vector<double> r0, omega;
+  bool have_ground = false, have_right = false, have_left = false;
+  bool cache_at_t = false;  // primal intermediates correspond to the converged t
+  double e_ccsd = 0.0;
+  std::string err;
+  // densities of the last pair
+  int dens_k = -1, dens_l = -1;
+  DevBuf Dd, Zd;
+};
+
+namespace {
+
+void sync(ccsd_ctx* c) { CUDA_OK(cudaStreamSynchronize(c->st)); }
+
+// G[p][q] = <X_p|Y_q> on the host
+std::vector<double> gram(ccsd_ctx* c, const double* X, int64_t ldx, int np, const double* Y, int64_t ldy, int nq) {
+  DevBuf G(np * nq);
+  double* work = c->ex->scratch(wdot_work_size(np, nq));
+  launch_wdot(c->vs, X, ldx, np, Y, ldy, nq, G.p, nq, work, c->st);
+  std::vector<double> h(np * nq);
+  CUDA_OK(cudaMemcpyAsync(h.data(), G.p, np * nq * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  sync(c);
+  return h;
+}
+
+double maxabs(ccsd_ctx* c, const double* x, int64_t n) {
+  DevBuf out(2);
+  launch_maxabs(n, x, out.p, c->ex->scratch(1024), c->st);
+  double r;
+  CUDA_OK(cudaMemcpyAsync(&r, out.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  sync(c);
+  return r;
+}
+
+// Y[q] = sum_p coef[p][q] X[p] (coef on host, row-major np x nq)
+void lincomb(ccsd_ctx* c, const double* X, int64_t ldx, int np, const std::vector<double>& coef, double* Y,
+             int64_t ldy, int nq, bool acc) {
+  DevBuf cd(np * nq);
+  CUDA_OK(cudaMemcpyAsync(cd.p, coef.data(), np * nq * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  launch_lincomb(c->vs, X, ldx, np, cd.p, nq, Y, ldy, nq, acc, c->st);
+  sync(c);  // coefficient buffer is released on return
+}
+
+// ---------------------------------------------------------------------------
+// program drivers
+// ---------------------------------------------------------------------------
+
+// Omega(t) -> om, energy (host).  Updates the cached primal intermediates.
+double forward(ccsd_ctx* c, const double* t, double* om) {
+  auto& cp = c->P.cp;
+  Executor& ex = *c->ex;
+  ex.set_nvec(1);
+  ex.bind(cp.t1, const_cast<double*>(t));
+  ex.bind(cp.t2, const_cast<double*>(t) + c->n1);
+  ex.bind(cp.O1, om);
+  ex.bind(cp.O2, om + c->n1);
+  ex.bind(cp.E, c->escal.p);
+  ex.run(cp.fwd_t);
+  double e;
+  CUDA_OK(cudaMemcpyAsync(&e, c->escal.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  sync(c);
+  c->cache_at_t = (t == c->t.p);
+  return e;
+}
+
+void ensure_cache(ccsd_ctx* c) {
+  if (!c->have_ground) throw Err(CCSD_ERR_STATE, "ground state not solved");
+  if (!c->cache_at_t) {
+    DevBuf om(c->dim);
+    forward(c, c->t.p, om.p);
+  }
+  auto& cp = c->P.cp;
+  c->ex->bind(cp.t1, c->t.p);
+  c->ex->bind(cp.t2, c->t.p + c->n1);
+}
+
+// Y = A X for nvec vectors ([nvec][dim])
+void right_block(ccsd_ctx* c, const double* X, double* Y, int nvec) {
+  ensure_cache(c);
+  Executor& ex = *c->ex;
+  auto& P = c->P;
+  ex.set_nvec(nvec);
+  ex.bind(P.zR1, const_cast<double*>(X), c->dim);
+  ex.bind(P.zR2, const_cast<double*>(X) + c->n1, c->dim);
+  ex.bind(P.zAR1, Y, c->dim);
+  ex.bind(P.zAR2, Y + c->n1, c->dim);
+  ex.bind(P.zAE, c->gsc.p);
+  ex.run(P.jvp_z);
+}
+
+// Y = (X^T A)^T for nvec vectors; with eseed != 0 adds eseed * eta (used for eta itself)
+void left_block(ccsd_ctx* c, const double* X, double* Y, int nvec, double eseed = 0.0) {
+  ensure_cache(c);
+  Executor& ex = *c->ex;
+  auto& P = c->P;
+  ex.set_nvec(nvec);
+  DevBuf W(nvec * c->dim), G(nvec * c->dim);
+  launch_weight(c->vs, X, W.p, nvec, c->dim, c->st);
+  std::vector<double> es(nvec, eseed);
+  CUDA_OK(cudaMemcpyAsync(c->seedE.p, es.data(), nvec * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  ex.bind(P.zL1, W.p, c->dim);
+  ex.bind(P.zL2, W.p + c->n1, c->dim);
+  ex.bind(P.zLE, c->seedE.p);
+  ex.bind(P.zLA1, G.p, c->dim);
+  ex.bind(P.zLA2, G.p + c->n1, c->dim);
+  ex.run(P.vjp_z);
+  launch_packed_grad(c->vs, G.p, Y, nvec, c->dim, c->st);
+  sync(c);
+}
+
+// y = sum_nu d^2(g0 E + <g|Omega>)/dt dt_nu r_nu (packed)
+void hess_right(ccsd_ctx* c, double g0, const double* g, const double* r, double* y) {
+  ensure_cache(c);
+  Executor& ex = *c->ex;
+  auto& P = c->P;
+  ex.set_nvec(1);
+  DevBuf W(c->dim), G(c->dim), s0(1);
+  launch_weight(c->vs, g, W.p, 1, c->dim, c->st);
+  CUDA_OK(cudaMemcpyAsync(s0.p, &g0, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  ex.bind(P.hG1, W.p);
+  ex.bind(P.hG2, W.p + c->n1);
+  ex.bind(P.hG0, s0.p);
+  ex.bind(P.hR1, const_cast<double*>(r));
+  ex.bind(P.hR2, const_cast<double*>(r) + c->n1);
+  ex.bind(P.hF1, G.p);
+  ex.bind(P.hF2, G.p + c->n1);
+  ex.run(P.hvp);
+  launch_packed_grad(c->vs, G.p, y, 1, c->dim, c->st);
+  sync(c);
+}
+
+// ---------------------------------------------------------------------------
+// DIIS
+// ---------------------------------------------------------------------------
+struct Diis {
+  ccsd_ctx* c;
+  int cap;
+  std::vector<std::unique_ptr<DevBuf>> X, E;
+  std::vector<double> Bm;  // cap x cap Gram matrix of stored errors
+  int m = 0, next = 0;
+  Diis(ccsd_ctx* c_, int cap_) : c(c_), cap(std::max(cap_, 1)), Bm(cap * cap, 0.0) {
+    for (int i = 0; i < cap; ++i) {
+      X.emplace_back(new DevBuf(c->dim));
+      E.emplace_back(new DevBuf(c->dim));
+    }
+  }
+  // store (x, e) and write the extrapolated vector to out
+  void step(const double* x, const double* e, double* out) {
+    int slot = next;
+    next = (next + 1) % cap;
+    m = std::min(m + 1, cap);
+    CUDA_OK(cudaMemcpyAsync(X[slot]->p, x, c->dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    CUDA_OK(cudaMemcpyAsync(E[slot]->p, e, c->dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    for (int q = 0; q < m; ++q) {
+      std::vector<double> d = gram(c, E[q]->p, c->dim, 1, E[slot]->p, c->dim, 1);
+      Bm[q * cap + slot] = Bm[slot * cap + q] = d[0];
+    }
+    if (m < 2) {
+      CUDA_OK(cudaMemcpyAsync(out, x, c->dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+      return;
+    }
+    int k = m + 1;
+    std::vector<double> A(k * k, 0.0), b(k, 0.0);
+    double scale = 0.0;
+    for (int i = 0; i < m; ++i) scale = std::max(scale, std::fabs(Bm[i * cap + i]));
+    if (scale == 0.0) scale = 1.0;
+    for (int i = 0; i < m; ++i) {
+      for (int j = 0; j < m; ++j) A[i * k + j] = Bm[i * cap + j] / scale;
+      A[i * k + m] = A[m * k + i] = -1.0;
+    }
+    b[m] = -1.0;
+    if (!lu_solve(k, A, b)) {
+      CUDA_OK(cudaMemcpyAsync(out, x, c->dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+      return;
+    }
+    // slots 0..m-1 hold the stored vectors (ring buffer, all valid once m == cap)
+    std::vector<double> coef(m);
+    for (int i = 0; i < m; ++i) coef[i] = b[i];
+    // gather pointers: X slots are separate buffers; combine one at a time
+    launch_axpby(c->dim, coef[0], X[0]->p, 0.0, out, c->st);
+    for (int i = 1; i < m; ++i) launch_axpby(c->dim, coef[i], X[i]->p, 1.0, out, c->st);
+  }
+};
+
+// Solve x^T A = -rhs^T by preconditioned Jacobi + DIIS; x holds the guess on entry
+int solve_left_linear(ccsd_ctx* c, const double* rhs, double* x, double tol) {
+  DevBuf res(c->dim), xn(c->dim);
+  Diis diis(c, c->opt.diis_dim);
+  for (int it = 1; it <= c->opt.max_iter; ++it) {
+    left_block(c, x, res.p, 1);
+    launch_axpby(c->dim, 1.0, rhs, 1.0, res.p, c->st);
+    double err = maxabs(c, res.p, c->dim);
+    if (!std::isfinite(err)) throw Err(CCSD_ERR_NOT_CONVERGED, "linear equations diverged");
+    if (err < tol) return it;
+    launch_precond(c->vs, c->eps.p, res.p, xn.p, 0.0, c->st);
+    launch_axpby(c->dim, 1.0, x, -1.0, xn.p, c->st);  // xn = x - res/D
+    diis.step(xn.p, res.p, x);
+  }
+  throw Err(CCSD_ERR_NOT_CONVERGED, "left linear equations not converged");
+}
+
+// ---------------------------------------------------------------------------
+// Davidson for the lowest nroots of A (side 0) or A^T (side 1)
+// ---------------------------------------------------------------------------
+int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std::vector<std::unique_ptr<DevBuf>>& out) {
+  const int64_t dim = c->dim;
+  const int maxsub = std::max(c->opt.davidson_max_sub, 3 * nroots);
+  const int block = std::max(1, std::min(c->opt.davidson_block, 16));
+  DevBuf V(maxsub * dim), AV(maxsub * dim);
+  int m = 0;
+  std::vector<double> Gm(maxsub * maxsub, 0.0);  // Gm[i][j] = <V_i | A V_j>
+  auto apply = [&](int first, int count) {
+    for (int s = 0; s < count; s += block) {
+      int nb = std::min(block, count - s);
+      double* X = V.p + (first + s) * dim;
+      double* Y = AV.p + (first + s) * dim;
+      if (side == 0)
+        right_block(c, X, Y, nb);
+      else
+        left_block(c, X, Y, nb);
+    }
+    // extend the projected matrix
+    std::vector<double> a = gram(c, V.p, dim, first + count, AV.p + first * dim, dim, count);
+    std::vector<double> b = gram(c, V.p + first * dim, dim, count, AV.p, dim, first);
+    for (int i = 0; i < first + count; ++i)
+      for (int j = 0; j < count; ++j) Gm[i * maxsub + first + j] = a[i * count + j];
+    for (int i = 0; i < count; ++i)
+      for (int j = 0; j < first; ++j) Gm[(first + i) * maxsub + j] = b[i * first + j];
+  };
+  // orthonormalise candidate vectors in place (slots m..m+cnt-1); returns number kept
+  auto orthonormalize = [&](int cnt) {
+    int kept = 0;
+    for (int q = 0; q < cnt; ++q) {
+      double* x = V.p + (m + q) * dim;
+      std::vector<double> nrm0 = gram(c, x, dim, 1, x, dim, 1);
+      if (!(nrm0[0] > 0.0)) continue;
+      launch_axpby(dim, 1.0 / std::sqrt(nrm0[0]), x, 0.0, x, c->st);
+      int have = m + kept;
+      for (int pass = 0; pass < 2; ++pass) {
+        if (have == 0) break;
+        std::vector<double> d = gram(c, V.p, dim, have, x, dim, 1);
+        std::vector<double> coef(have);
+        for (int i = 0; i < have; ++i) coef[i] = -d[i];
+        lincomb(c, V.p, dim, have, coef, x, dim, 1, true);
+      }
+      std::vector<double> nrm = gram(c, x, dim, 1, x, dim, 1);
+      if (nrm[0] < 1e-16) continue;
+      double* dst = V.p + (m + kept) * dim;
+      launch_axpby(dim, 1.0 / std::sqrt(nrm[0]), x, 0.0, dst, c->st);
+      ++kept;
+    }
+    return kept;
+  };
+  // guesses: singles unit vectors of the lowest orbital-energy differences
+  {
+    std::vector<double> eps(c->n);
+    CUDA_OK(cudaMemcpy(eps.data(), c->eps.p, c->n * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<std::pair<double, int>> d1;
+    for (int i = 0; i < c->o; ++i)
+      for (int a = 0; a < c->v; ++a) d1.push_back({eps[c->o + a] - eps[i], i * c->v + a});
+    std::stable_sort(d1.begin(), d1.end(), [](auto& x, auto& y) { return x.first < y.first; });
+    int ng = std::min<int>(nroots, (int)d1.size());
+    CUDA_OK(cudaMemsetAsync(V.p, 0, ng * dim * sizeof(double), c->st));
+    for (int g = 0; g < ng; ++g) {
+      double one = 1.0;
+      CUDA_OK(cudaMemcpyAsync(V.p + g * dim + d1[g].second, &one, sizeof(double), cudaMemcpyHostToDevice, c->st));
+      sync(c);
+    }
+    int kept = orthonormalize(ng);
+    apply(0, kept);
+    m = kept;
+  }
+  DevBuf X(nroots * dim), AX(nroots * dim), Rz(nroots * dim);
+  for (int it = 1; it <= c->opt.max_iter; ++it) {
+    std::vector<double> G(m * m);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) G[i * m + j] = Gm[i * maxsub + j];
+    std::vector<std::complex<double>> ev = eigenvalues(m, G);
+    std::sort(ev.begin(), ev.end(), [](auto& a, auto& b) { return a.real() < b.real(); });
+    if ((int)ev.size() < nroots) throw Err(CCSD_ERR_NOT_CONVERGED, "subspace too small");
+    double scale = 0.0;
+    for (auto& e : ev) scale = std::max(scale, std::abs(e));
+    for (int k = 0; k < nroots; ++k)
+      if (std::fabs(ev[k].imag()) > 1e-9 * std::max(scale, 1.0))
+        throw Err(CCSD_ERR_COMPLEX_ROOT, "complex eigenvalue among the wanted roots");
+    std::vector<double> U(m * nroots);
+    omega.assign(nroots, 0.0);
+    for (int k = 0; k < nroots; ++k) {
+      omega[k] = ev[k].real();
+      std::vector<double> u = eigenvector(m, G, omega[k]);
+      for (int i = 0; i < m; ++i) U[i * nroots + k] = u[i];
+    }
+    lincomb(c, V.p, dim, m, U, X.p, dim, nroots, false);
+    lincomb(c, AV.p, dim, m, U, AX.p, dim, nroots, false);
+    // residuals r_k = A x_k - omega_k x_k (x_k has unit norm up to roundoff)
+    std::vector<double> xn = gram(c, X.p, dim, nroots, X.p, dim, nroots);
+    std::vector<int> todo;
+    for (int k = 0; k < nroots; ++k) {
+      double s = 1.0 / std::sqrt(xn[k * nroots + k]);
+      launch_axpby(dim, s, X.p + k * dim, 0.0, X.p + k * dim, c->st);
+      launch_axpby(dim, s, AX.p + k * dim, 0.0, AX.p + k * dim, c->st);
+      launch_axpby(dim, 1.0, AX.p + k * dim, 0.0, Rz.p + k * dim, c->st);
+      launch_axpby(dim, -omega[k], X.p + k * dim, 1.0, Rz.p + k * dim, c->st);
+    }
+    std::vector<double> rn = gram(c, Rz.p, dim, nroots, Rz.p, dim, nroots);
+    for (int k = 0; k < nroots; ++k)
+      if (std::sqrt(std::max(rn[k * nroots + k], 0.0)) > c->opt.tol_eom) todo.push_back(k);
+    if (todo.empty()) {
+      out.clear();
+      for (int k = 0; k < nroots; ++k) {
+        out.emplace_back(new DevBuf(dim));
+        CUDA_OK(cudaMemcpyAsync(out[k]->p, X.p + k * dim, dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+      }
+      sync(c);
+      return it;
+    }
+    if (m + (int)todo.size() > maxsub) {  // restart from the current Ritz vectors
+      CUDA_OK(cudaMemcpyAsync(V.p, X.p, nroots * dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+      m = 0;
+      int kept = orthonormalize(nroots);
+      std::fill(Gm.begin(), Gm.end(), 0.0);
+      apply(0, kept);
+      m = kept;
+    }
+    for (size_t q = 0; q < todo.size(); ++q) {
+      int k = todo[q];
+      launch_precond(c->vs, c->eps.p, Rz.p + k * dim, V.p + (m + q) * dim, omega[k], c->st);
+    }
+    int kept = orthonormalize((int)todo.size());
+    if (kept == 0) throw Err(CCSD_ERR_NOT_CONVERGED, "Davidson stagnated");
+    apply(m, kept);
+    m += kept;
+  }
+  throw Err(CCSD_ERR_NOT_CONVERGED, "Davidson not converged");
+}
+
+// normalise R to unit packed norm, largest-magnitude component positive
+void normalize_right(ccsd_ctx* c, double* R) {
+  std::vector<double> nr = gram(c, R, c->dim, 1, R, c->dim, 1);
+  launch_axpby(c->dim, 1.0 / std::sqrt(nr[0]), R, 0.0, R, c->st);
+  DevBuf o2(2);
+  launch_argmaxabs(c->dim, R, o2.p, c->ex->scratch(1024), c->st);
+  double h2[2];
+  CUDA_OK(cudaMemcpyAsync(h2, o2.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  sync(c);
+  if (h2[1] < 0) launch_axpby(c->dim, -1.0, R, 0.0, R, c->st);
+}
+
+ccsd_status fail(ccsd_ctx* c, ccsd_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+template <typename F>
+ccsd_status guarded(ccsd_ctx* c, F&& f) {
+  if (!c) return CCSD_ERR_ARG;
+  try {
+    f();
+    return CCSD_OK;
+  } catch (const Err& e) {
+    return fail(c, e.code, e.what());
+  } catch (const std::bad_alloc& e) {
+    return fail(c, CCSD_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    std::string m = e.what();
+    if (m.find("out of memory") != std::string::npos) return fail(c, CCSD_ERR_OOM, m);
+    return fail(c, CCSD_ERR_CUDA, m);
+  }
+}
+
+// copy n doubles from a host or device pointer into a new device buffer
+void to_device(ccsd_ctx* c, const double* src, int64_t n, DevBuf& dst) {
+  dst.alloc(n);
+  CUDA_OK(cudaMemcpyAsync(dst.p, src, n * sizeof(double), cudaMemcpyDefault, c->st));
+}
+
+void from_device(ccsd_ctx* c, const double* src, int64_t n, double* dst) {
+  CUDA_OK(cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDefault, c->st));
+}
+
+// left state k: (l0, L) with L a device vector (k = 0: lambda)
+const double* left_vec(ccsd_ctx* c, int k) { return k == 0 ? c->lam.p : c->L[k - 1]->p; }
+double omega_of(ccsd_ctx* c, int k) { return k == 0 ? 0.0 : c->omega[k - 1]; }
+
+void compute_densities(ccsd_ctx* c, int k, int l) {
+  const int nr = (int)c->omega.size();
+  if (k < 0 || l < 0 || k == l) throw Err(CCSD_ERR_ARG, "state indices must differ and be >= 0");
+  if (k > nr || l > nr) throw Err(CCSD_ERR_ARG, "state index beyond the solved roots");
+  if ((k > 0 || l > 0) && !(c->have_right && c->have_left)) throw Err(CCSD_ERR_STATE, "EOM states not solved");
+  if (c->dens_k == k && c->dens_l == l) return;
+  ensure_cache(c);
+  const int64_t dim = c->dim;
+  auto& P = c->P;
+  Executor& ex = *c->ex;
+  if (!c->Dd.p) c->Dd.alloc((int64_t)c->n * c->n);
+  if (!c->Zd.p) c->Zd.alloc((int64_t)c->naux * c->n * c->n);
+  DevBuf zeta(dim), Wz(dim);
+  if (l == 0) {
+    // zeta = L_k / (E_0 - E_k) = -L_k / omega_k  (Eqs. for the ground-state right state)
+    launch_axpby(dim, -1.0 / c->omega[k - 1], c->L[k - 1]->p, 0.0, zeta.p, c->st);
+    launch_weight(c->vs, zeta.p, Wz.p, 1, dim, c->st);
+    ex.set_nvec(1);
+    ex.bind(P.eZ1, Wz.p);
+    ex.bind(P.eZ2, Wz.p + c->n1);
+    ex.bind(P.eH, c->Dd.p);
+    ex.bind(P.eB, c->Zd.p);
+    ex.run(P.dens0);
+  } else {
+    double dw = omega_of(c, l) - omega_of(c, k);
+    if (std::fabs(dw) < c->opt.tol_degen) throw Err(CCSD_ERR_DEGENERATE, "omega_l - omega_k below threshold");
+    const double l0 = (k == 0) ? 1.0 : 0.0;
+    const double g0 = l0 / dw;
+    const double* Rl = c->R[l - 1]->p;
+    const double r0 = c->r0[l - 1];
+    DevBuf gam(dim), teta(dim), hv(dim), Wg(dim), s0(1);
+    launch_axpby(dim, 1.0 / dw, left_vec(c, k), 0.0, gam.p, c->st);
+    // t-eta = <L_k|tau|R_l> + d^2(g0 E + gamma.Omega)/dt^2 R_l
+    launch_tau_expectation(c->vs, r0, left_vec(c, k), Rl, teta.p, c->st);
+    hess_right(c, g0, gam.p, Rl, hv.p);
+    launch_axpby(dim, 1.0, hv.p, 1.0, teta.p, c->st);
+    // zeta^T A = -t-eta^T (Eq. amplituderelax)
+    launch_precond(c->vs, c->eps.p, teta.p, zeta.p, 0.0, c->st);
+    launch_axpby(dim, 0.0, zeta.p, -1.0, zeta.p, c->st);
+    solve_left_linear(c, teta.p, zeta.p, c->opt.tol_lin);
+    launch_weight(c->vs, zeta.p, Wz.p, 1, dim, c->st);
+    launch_weight(c->vs, gam.p, Wg.p, 1, dim, c->st);
+    CUDA_OK(cudaMemcpyAsync(s0.p, &g0, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    ensure_cache(c);
+    ex.set_nvec(1);
+    ex.bind(P.dZ1, Wz.p);
+    ex.bind(P.dZ2, Wz.p + c->n1);
+    ex.bind(P.dG1, Wg.p);
+    ex.bind(P.dG2, Wg.p + c->n1);
+    ex.bind(P.dG0, s0.p);
+    ex.bind(P.dR1, const_cast<double*>(Rl));
+    ex.bind(P.dR2, const_cast<double*>(Rl) + c->n1);
+    ex.bind(P.dH, c->Dd.p);
+    ex.bind(P.dB, c->Zd.p);
+    ex.run(P.dens1);
+  }
+  sync(c);
+  c->dens_k = k;
+  c->dens_l = l;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ccsd_default_options(ccsd_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = CCSD_PREC_FP64;
+  opt->splits = 3;
+  opt->relax_orbitals = 0;
+  opt->tol_res = 1e-10;
+  opt->tol_eom = 1e-7;
+  opt->tol_lin = 1e-9;
+  opt->tol_degen = 1e-8;
+  opt->max_iter = 100;
+  opt->diis_dim = 8;
+  opt->davidson_block = 8;
+  opt->davidson_max_sub = 48;
+  opt->guess = CCSD_GUESS_MP2;
+  opt->stream = nullptr;
+}
+
+const char* ccsd_strerror(ccsd_status s) {
+  switch (s) {
+    case CCSD_OK: return "ok";
+    case CCSD_ERR_ARG: return "invalid argument";
+    case CCSD_ERR_OOM: return "out of device memory";
+    case CCSD_ERR_CUDA: return "CUDA error";
+    case CCSD_ERR_STATE: return "prerequisite call missing";
+    case CCSD_ERR_NOT_CONVERGED: return "not converged";
+    case CCSD_ERR_COMPLEX_ROOT: return "complex EOM root";
+    case CCSD_ERR_DEGENERATE: return "degenerate states";
+    case CCSD_ERR_NOT_HF: return "reference is not Hartree-Fock";
+    case CCSD_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* ccsd_last_error(ccsd_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int o, int v, int naux,
+                        const ccsd_options* opt, ccsd_handle* out) {
+  if (!out) return CCSD_ERR_ARG;
+  *out = nullptr;
+  if (!eps || !h || !B || o < 1 || v < 1 || naux < 1) return CCSD_ERR_ARG;
+  ccsd_ctx* c = new (std::nothrow) ccsd_ctx();
+  if (!c) return CCSD_ERR_OOM;
+  if (opt)
+    c->opt = *opt;
+  else
+    ccsd_default_options(&c->opt);
+  if (c->opt.relax_orbitals) {
+    delete c;
+    return CCSD_ERR_ARG;
+  }
+  ccsd_status s = guarded(c, [&] {
+    c->o = o;
+    c->v = v;
+    c->naux = naux;
+    c->n = o + v;
+    c->vs = VecShape{o, v};
+    c->n1 = (int64_t)o * v;
+    c->dim = c->vs.dim();
+    c->st = (cudaStream_t)c->opt.stream;
+    // symmetry of the inputs
+    {
+      const int64_t n = c->n;
+      std::vector<double> hh(n * n), Bh((int64_t)naux * n * n);
+      CUDA_OK(cudaMemcpy(hh.data(), h, n * n * sizeof(double), cudaMemcpyDefault));
+      CUDA_OK(cudaMemcpy(Bh.data(), B, (int64_t)naux * n * n * sizeof(double), cudaMemcpyDefault));
+      double scale = 1e-300, asym = 0.0;
+      for (int64_t J = 0; J <= naux; ++J) {
+        const double* m = (J == naux) ? hh.data() : Bh.data() + J * n * n;
+        for (int64_t p = 0; p < n; ++p)
+          for (int64_t q = 0; q < p; ++q) {
+            asym = std::max(asym, std::fabs(m[p * n + q] - m[q * n + p]));
+            scale = std::max(scale, std::fabs(m[p * n + q]));
+          }
+      }
+      for (double x : hh)
+        if (!std::isfinite(x)) throw Err(CCSD_ERR_ARG, "non-finite h");
+      for (double x : Bh)
+        if (!std::isfinite(x)) throw Err(CCSD_ERR_ARG, "non-finite B");
+      if (asym > 1e-10 * std::max(1.0, scale)) throw Err(CCSD_ERR_ARG, "h or B is not symmetric in pq");
+    }
+    to_device(c, eps, c->n, c->eps);
+    to_device(c, h, (int64_t)c->n * c->n, c->h);
+    to_device(c, B, (int64_t)naux * c->n * c->n, c->B);
+    c->t.alloc(c->dim);
+    c->lam.alloc(c->dim);
+    c->eta.alloc(c->dim);
+    c->escal.alloc(16);
+    c->seedE.alloc(16);
+    c->gsc.alloc(16);
+    CUDA_OK(cudaMemsetAsync(c->t.p, 0, c->dim * sizeof(double), c->st));
+    std::vector<double> ones(o, 1.0);
+    c->ones.alloc(o);
+    CUDA_OK(cudaMemcpyAsync(c->ones.p, ones.data(), o * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    build_programs(c->P);
+    auto& cp = c->P.cp;
+    c->ex.reset(new Executor(cp.g, o, v, naux, 16, c->st));
+    Executor& ex = *c->ex;
+    ex.set_precision(c->opt.precision, c->opt.splits);
+    ex.bind(cp.h, c->h.p);
+    ex.bind(cp.B, c->B.p);
+    ex.bind(cp.ones_o, c->ones.p);
+    // persistent storage for everything the forward program writes (primal cache)
+    for (const Op& op : cp.fwd) {
+      int t = op.out.t;
+      if (t == cp.O1 || t == cp.O2 || t == cp.E) continue;
+      ex.alloc_persistent(t);
+    }
+    ex.run(cp.fwd_const);
+    sync(c);
+  });
+  if (s != CCSD_OK) {
+    delete c;
+    return s;
+  }
+  *out = c;
+  return CCSD_OK;
+}
+
+void ccsd_destroy(ccsd_handle h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  else cudaDeviceSynchronize();
+  delete h;
+}
+
+ccsd_status ccsd_residual(ccsd_handle c, const double* t, double* omega, double* e) {
+  return guarded(c, [&] {
+    if (!t || !omega) throw Err(CCSD_ERR_ARG, "null pointer");
+    DevBuf td, od(c->dim);
+    to_device(c, t, c->dim, td);
+    double en = forward(c, td.p, od.p);
+    c->cache_at_t = false;
+    from_device(c, od.p, c->dim, omega);
+    sync(c);
+    if (e) *e = en;
+  });
+}
+
+ccsd_status ccsd_solve_ground(ccsd_handle c, double* e_ccsd, int* iters) {
+  return guarded(c, [&] {
+    const int64_t dim = c->dim;
+    DevBuf om(dim), tn(dim);
+    Diis diis(c, c->opt.diis_dim);
+    CUDA_OK(cudaMemsetAsync(c->t.p, 0, dim * sizeof(double), c->st));
+    c->have_ground = c->have_right = c->have_left = false;
+    c->dens_k = c->dens_l = -1;
+    int it = 1;
+    double e = 0.0;
+    for (;; ++it) {
+      if (it > c->opt.max_iter) throw Err(CCSD_ERR_NOT_CONVERGED, "ground state not converged");
+      e = forward(c, c->t.p, om.p);
+      double err = maxabs(c, om.p, dim);
+      if (!std::isfinite(err) || !std::isfinite(e)) throw Err(CCSD_ERR_NOT_CONVERGED, "ground state diverged");
+      if (err < c->opt.tol_res) break;
+      launch_precond(c->vs, c->eps.p, om.p, tn.p, 0.0, c->st);
+      launch_axpby(dim, 1.0, c->t.p, -1.0, tn.p, c->st);  // tn = t - Omega/D
+      diis.step(tn.p, om.p, c->t.p);
+      c->cache_at_t = false;
+    }
+    c->e_ccsd = e;
+    c->have_ground = true;
+    // eta = dE/dt and the ground-state multipliers lambda^T A = -eta^T
+    DevBuf zero(dim);
+    CUDA_OK(cudaMemsetAsync(zero.p, 0, dim * sizeof(double), c->st));
+    left_block(c, zero.p, c->eta.p, 1, 1.0);
+    launch_precond(c->vs, c->eps.p, c->eta.p, c->lam.p, 0.0, c->st);
+    launch_axpby(dim, 0.0, c->lam.p, -1.0, c->lam.p, c->st);
+    solve_left_linear(c, c->eta.p, c->lam.p, c->opt.tol_lin);
+    if (e_ccsd) *e_ccsd = e;
+    if (iters) *iters = it;
+  });
+}
+
+ccsd_status eom_solve_right(ccsd_handle c, int nroots, double* omega, int* iters) {
+  return guarded(c, [&] {
+    if (nroots < 1 || nroots > c->n1) throw Err(CCSD_ERR_ARG, "bad nroots");
+    if (!c->have_ground) throw Err(CCSD_ERR_STATE, "ground state not solved");
+    std::vector<double> w;
+    int it = davidson(c, 0, nroots, w, c->R);
+    c->omega = w;
+    c->r0.assign(nroots, 0.0);
+    for (int k = 0; k < nroots; ++k) {
+      normalize_right(c, c->R[k]->p);
+      std::vector<double> d = gram(c, c->eta.p, c->dim, 1, c->R[k]->p, c->dim, 1);
+      c->r0[k] = d[0] / w[k];
+    }
+    c->have_right = true;
+    c->have_left = false;
+    c->dens_k = c->dens_l = -1;
+    if (omega) std::copy(w.begin(), w.end(), omega);
+    if (iters) *iters = it;
+  });
+}
+
+ccsd_status eom_solve_left(ccsd_handle c, int nroots, double* omega, int* iters) {
+  return guarded(c, [&] {
+    if (!c->have_right) throw Err(CCSD_ERR_STATE, "eom_solve_right first");
+    if (nroots != (int)c->omega.size()) throw Err(CCSD_ERR_ARG, "nroots differs from the right solve");
+    std::vector<double> w;
+    std::vector<std::unique_ptr<DevBuf>> Lr;
+    int it = davidson(c, 1, nroots, w, Lr);
+    for (int k = 0; k < nroots; ++k)
+      if (std::fabs(w[k] - c->omega[k]) > 1e-5 * std::max(1.0, std::fabs(c->omega[k])))
+        throw Err(CCSD_ERR_NOT_CONVERGED, "left and right roots differ");
+    // biorthonormalise: L_new_k = sum_m Minv^T[k][m] L_m with M[m][l] = <L_m|R_l>
+    std::vector<double> M(nroots * nroots);
+    for (int k = 0; k < nroots; ++k)
+      for (int l = 0; l < nroots; ++l) M[k * nroots + l] = gram(c, Lr[k]->p, c->dim, 1, c->R[l]->p, c->dim, 1)[0];
+    std::vector<double> Minv;
+    if (!invert(nroots, M, Minv)) throw Err(CCSD_ERR_DEGENERATE, "left/right overlap matrix is singular");
+    c->L.clear();
+    for (int k = 0; k < nroots; ++k) {
+      c->L.emplace_back(new DevBuf(c->dim));
+      CUDA_OK(cudaMemsetAsync(c->L[k]->p, 0, c->dim * sizeof(double), c->st));
+      for (int m = 0; m < nroots; ++m)
+        launch_axpby(c->dim, Minv[k * nroots + m], Lr[m]->p, 1.0, c->L[k]->p, c->st);
+    }
+    sync(c);
+    c->have_left = true;
+    c->dens_k = c->dens_l = -1;
+    if (omega) std::copy(w.begin(), w.end(), omega);
+    if (iters) *iters = it;
+  });
+}
+
+ccsd_status ccsd_jacobian_transform(ccsd_handle c, int side, int nvec, const double* x, double* y) {
+  return guarded(c, [&] {
+    if ((side != 0 && side != 1) || nvec < 1 || !x || !y) throw Err(CCSD_ERR_ARG, "bad arguments");
+    const int64_t dim = c->dim;
+    DevBuf xd, yd;
+    const double* xp = x;
+    double* yp = y;
+    bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
+    if (!xdev) {
+      to_device(c, x, nvec * dim, xd);
+      xp = xd.p;
+    }
+    if (!ydev) {
+      yd.alloc(nvec * dim);
+      yp = yd.p;
+    }
+    const int block = 16;
+    for (int s = 0; s < nvec; s += block) {
+      int nb = std::min(block, nvec - s);
+      if (side == 0)
+        right_block(c, xp + s * dim, yp + s * dim, nb);
+      else
+        left_block(c, xp + s * dim, yp + s * dim, nb);
+    }
+    if (!ydev) from_device(c, yp, nvec * dim, y);
+    sync(c);
+  });
+}
+
+ccsd_status ccsd_get_amplitudes(ccsd_handle c, double* t, double* lambda) {
+  return guarded(c, [&] {
+    if (!c->have_ground) throw Err(CCSD_ERR_STATE, "ground state not solved");
+    if (t) from_device(c, c->t.p, c->dim, t);
+    if (lambda) from_device(c, c->lam.p, c->dim, lambda);
+    sync(c);
+  });
+}
+
+ccsd_status ccsd_get_states(ccsd_handle c, int nroots, double* r0, double* right, double* left) {
+  return guarded(c, [&] {
+    if (!c->have_right) throw Err(CCSD_ERR_STATE, "EOM states not solved");
+    if (nroots < 1 || nroots > (int)c->omega.size()) throw Err(CCSD_ERR_ARG, "bad nroots");
+    if (left && !c->have_left) throw Err(CCSD_ERR_STATE, "left states not solved");
+    for (int k = 0; k < nroots; ++k) {
+      if (r0) r0[k] = c->r0[k];
+      if (right) from_device(c, c->R[k]->p, c->dim, right + k * c->dim);
+      if (left) from_device(c, c->L[k]->p, c->dim, left + k * c->dim);
+    }
+    sync(c);
+  });
+}
+
+ccsd_status ccsd_coupling_densities(ccsd_handle c, int k, int l, double* D, double* Z) {
+  return guarded(c, [&] {
+    compute_densities(c, k, l);
+    if (D) from_device(c, c->Dd.p, (int64_t)c->n * c->n, D);
+    if (Z) from_device(c, c->Zd.p, (int64_t)c->naux * c->n * c->n, Z);
+    sync(c);
+  });
+}
+
+ccsd_status ccsd_derivative_coupling(ccsd_handle c, int k, int l, int ndir, const double* dh, const double* dB,
+                                     double* F) {
+  return guarded(c, [&] {
+    if (ndir < 1 || !dh || !dB || !F) throw Err(CCSD_ERR_ARG, "bad arguments");
+    compute_densities(c, k, l);
+    const int64_t nn = (int64_t)c->n * c->n, nb = (int64_t)c->naux * nn;
+    DevBuf out(2), tmp;
+    bool hdev = is_device_ptr(dh), bdev = is_device_ptr(dB);
+    double* work = c->ex->scratch(1024);
+    for (int d = 0; d < ndir; ++d) {
+      double fh, fb;
+      const double* hp = dh + d * nn;
+      if (!hdev) {
+        to_device(c, hp, nn, tmp);
+        hp = tmp.p;
+      }
+      launch_dot(nn, c->Dd.p, hp, out.p, work, c->st);
+      CUDA_OK(cudaMemcpyAsync(&fh, out.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      sync(c);
+      const double* bp = dB + d * nb;
+      if (!bdev) {
+        to_device(c, bp, nb, tmp);
+        bp = tmp.p;
+      }
+      launch_dot(nb, c->Zd.p, bp, out.p, work, c->st);
+      CUDA_OK(cudaMemcpyAsync(&fb, out.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+      sync(c);
+      F[d] = fh + fb;
+    }
+  });
+}
+
+ccsd_status ccsd_stats(ccsd_handle c, double* flops_fp64, double* flops_tc, long long* gemms, long long* tc_gemms) {
+  return guarded(c, [&] {
+    if (flops_fp64) *flops_fp64 = c->ex->stats.gemm_flops;
+    if (flops_tc) *flops_tc = c->ex->stats.tc_flops;
+    if (gemms) *gemms = c->ex->stats.gemm_calls;
+    if (tc_gemms) *tc_gemms = c->ex->stats.tc_calls;
+  });
+}
+
+long long ccsd_describe_program(const char* which, char* buf, size_t len) {
+  try {
+    Programs P;
+    build_programs(P);
+    const Prog* p = nullptr;
+    std::string w = which ? which : "";
+    if (w == "fwd") p = &P.cp.fwd;
+    else if (w == "jvp") p = &P.jvp_z;
+    else if (w == "vjp") p = &P.vjp_z;
+    else if (w == "hvp") p = &P.hvp;
+    else if (w == "dens1") p = &P.dens1;
+    else if (w == "dens0") p = &P.dens0;
+    if (!p) return -1;
+    std::string s = dump(P.cp.g, *p);
+    if (buf && len > 0) {
+      size_t m = std::min(len - 1, s.size());
+      std::memcpy(buf, s.data(), m);
+      buf[m] = 0;
+    }
+    return (long long)s.size();
+  } catch (...) {
+    return -1;
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,442 @@
+// Program executor: label analysis, operand gathering, GEMM dispatch.
+#include "exec.h"
+
+#include <algorithm>
+#include <map>
+#include <stdexcept>
+
+namespace ccsd {
+
+#define CK(x)                                                                                   \
+  do {                                                                                          \
+    cudaError_t e_ = (x);                                                                       \
+    if (e_ != cudaSuccess) throw std::runtime_error(std::string(#x ": ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+Executor::Executor(const Graph& g, int o, int v, int naux, int nvec_max, cudaStream_t st)
+    : g_(g), o_(o), v_(v), naux_(naux), nvec_max_(nvec_max), nvec_(1), st_(st) {
+  ts_.resize(g.T.size());
+}
+
+Executor::~Executor() {
+  clear_cache();
+  for (auto& t : ts_)
+    if (t.owned && t.p) cudaFree(t.p);
+  if (scratch_) cudaFree(scratch_);
+}
+
+void Executor::set_nvec(int nvec) {
+  if (nvec < 1 || nvec > nvec_max_) throw std::runtime_error("nvec out of range");
+  nvec_ = nvec;
+}
+
+int64_t Executor::extent(char c) const {
+  switch (c) {
+    case 'o': return o_;
+    case 'v': return v_;
+    case 'n': return o_ + v_;
+    case 'x': return naux_;
+    case 'z': return nvec_;
+  }
+  throw std::runtime_error(std::string("bad class ") + c);
+}
+
+int64_t Executor::numel(int t) const {
+  int64_t n = 1;
+  for (char c : g_.T[t].cls) n *= extent(c);
+  return n;
+}
+
+void Executor::bind(int t, double* p, int64_t zstride) {
+  TS& s = ts_[t];
+  if (s.owned && s.p) CK(cudaFree(s.p));
+  s.p = p;
+  s.owned = false;
+  s.bound = true;
+  s.zstride = zstride;
+}
+
+void Executor::unbind(int t) {
+  TS& s = ts_[t];
+  if (s.bound) {
+    s.p = nullptr;
+    s.bound = false;
+    s.zstride = -1;
+  }
+}
+
+void Executor::alloc_persistent(int t) {
+  TS& s = ts_[t];
+  if (s.p) return;
+  int64_t n = 1;
+  for (char c : g_.T[t].cls) n *= (c == 'z') ? nvec_max_ : extent(c);
+  CK(cudaMalloc(&s.p, std::max<int64_t>(n, 1) * sizeof(double)));
+  CK(cudaMemsetAsync(s.p, 0, std::max<int64_t>(n, 1) * sizeof(double), st_));
+  s.owned = true;
+}
+
+double* Executor::scratch(int64_t n) {
+  if (n > scratch_n_) {
+    if (scratch_) CK(cudaFree(scratch_));
+    CK(cudaMalloc(&scratch_, n * sizeof(double)));
+    scratch_n_ = n;
+  }
+  return scratch_;
+}
+
+double* Executor::tmp_alloc(int64_t n) {
+  void* p = nullptr;
+  CK(cudaMallocAsync(&p, std::max<int64_t>(n, 1) * sizeof(double), st_));
+  return (double*)p;
+}
+
+void Executor::tmp_free(double* p) {
+  if (p) CK(cudaFreeAsync(p, st_));
+}
+
+Executor::SView Executor::resolve(const Ref& r) const {
+  const std::string& cls = g_.T[r.t].cls;
+  const TS& s = ts_[r.t];
+  if (!s.p) throw std::runtime_error("tensor without storage: " + g_.T[r.t].name);
+  SView v;
+  v.nd = (int)cls.size();
+  if (v.nd > kMaxDims) throw std::runtime_error("too many dims");
+  if ((int)r.blk.size() != v.nd) throw std::runtime_error("block spec mismatch for " + g_.T[r.t].name);
+  int64_t full[kMaxDims];
+  for (int d = 0; d < v.nd; ++d) full[d] = extent(cls[d]);
+  if (v.nd > 0) {
+    v.str[v.nd - 1] = 1;
+    for (int d = v.nd - 2; d >= 0; --d) v.str[d] = v.str[d + 1] * full[d + 1];
+    if (cls[0] == 'z' && s.zstride >= 0) v.str[0] = s.zstride;
+  }
+  int64_t off = 0;
+  for (int d = 0; d < v.nd; ++d) {
+    v.ext[d] = full[d];
+    if (cls[d] == 'n') {
+      if (r.blk[d] == 'o') {
+        v.ext[d] = o_;
+      } else if (r.blk[d] == 'v') {
+        v.ext[d] = v_;
+        off += (int64_t)o_ * v.str[d];
+      }
+    }
+  }
+  v.base = s.p + off;
+  return v;
+}
+
+std::vector<Executor::Lab> Executor::merge(const SView& v, const std::string& lab) const {
+  if ((int)lab.size() != v.nd) throw std::runtime_error("label count mismatch");
+  std::vector<Lab> out;
+  for (int d = 0; d < v.nd; ++d) {
+    bool found = false;
+    for (auto& l : out)
+      if (l.c == lab[d]) {
+        if (l.e != v.ext[d]) throw std::runtime_error("diagonal extent mismatch");
+        l.s += v.str[d];
+        found = true;
+      }
+    if (!found) out.push_back(Lab{lab[d], v.ext[d], v.str[d]});
+  }
+  return out;
+}
+
+void Executor::zero_tensor(int t) {
+  const std::string& cls = g_.T[t].cls;
+  const TS& s = ts_[t];
+  int64_t n = numel(t);
+  bool contig = !(cls.size() > 0 && cls[0] == 'z' && s.zstride >= 0 && s.zstride != n / nvec_);
+  if (contig) {
+    CK(cudaMemsetAsync(s.p, 0, std::max<int64_t>(n, 1) * sizeof(double), st_));
+    return;
+  }
+  Strided sp;
+  sp.ndim = 2;
+  sp.ext[0] = nvec_;
+  sp.ext[1] = n / nvec_;
+  sp.s0[0] = s.zstride;
+  sp.s0[1] = 1;
+  sp.s1[0] = sp.s1[1] = 0;
+  launch_zero_strided(s.p, sp, st_);
+}
+
+static bool has(const std::vector<char>& v, char c) { return std::find(v.begin(), v.end(), c) != v.end(); }
+
+// Collapse a group of labels (in the given order) of a view into one stride.
+static bool collapse(const std::vector<char>& group, const std::map<char, std::pair<int64_t, int64_t>>& es,
+                     int64_t& stride) {
+  if (group.empty()) {
+    stride = 0;
+    return true;
+  }
+  // drop extent-1 labels: they do not constrain the layout
+  std::vector<std::pair<int64_t, int64_t>> g;
+  for (char c : group) {
+    auto& p = es.at(c);
+    if (p.first != 1) g.push_back(p);
+  }
+  if (g.empty()) {
+    stride = 0;
+    return true;
+  }
+  for (size_t i = 0; i + 1 < g.size(); ++i)
+    if (g[i].second != g[i + 1].second * g[i + 1].first) return false;
+  stride = g.back().second;
+  return true;
+}
+
+void Executor::exec_contract(const Op& op) {
+  SView O = resolve(op.out), A = resolve(op.a), B = resolve(op.b);
+  auto lo = merge(O, op.lo), la = merge(A, op.la), lb = merge(B, op.lb);
+  std::map<char, std::pair<int64_t, int64_t>> eo, ea, eb;
+  std::vector<char> co, ca, cb;
+  for (auto& l : lo) {
+    eo[l.c] = {l.e, l.s};
+    co.push_back(l.c);
+  }
+  for (auto& l : la) {
+    ea[l.c] = {l.e, l.s};
+    ca.push_back(l.c);
+  }
+  for (auto& l : lb) {
+    eb[l.c] = {l.e, l.s};
+    cb.push_back(l.c);
+  }
+  std::vector<char> bat, Ml, Nl, Kl;
+  for (char c : co) {
+    bool ia = has(ca, c), ib = has(cb, c);
+    if (ia && ib)
+      bat.push_back(c);
+    else if (ia)
+      Ml.push_back(c);
+    else if (ib)
+      Nl.push_back(c);
+    else
+      throw std::runtime_error("output label not in operands");
+  }
+  for (char c : ca)
+    if (!has(co, c)) {
+      if (!has(cb, c)) throw std::runtime_error("label summed over one operand");
+      Kl.push_back(c);
+    }
+  for (char c : cb)
+    if (!has(co, c) && !has(ca, c)) throw std::runtime_error("label summed over one operand");
+  auto ext_of = [&](char c) -> int64_t {
+    int64_t e = eo.count(c) ? eo[c].first : ea.count(c) ? ea[c].first : eb[c].first;
+    if ((eo.count(c) && eo[c].first != e) || (ea.count(c) && ea[c].first != e) || (eb.count(c) && eb[c].first != e))
+      throw std::runtime_error("label extent mismatch");
+    return e;
+  };
+  int64_t Bt = 1, M = 1, N = 1, K = 1;
+  for (char c : bat) Bt *= ext_of(c);
+  for (char c : Ml) M *= ext_of(c);
+  for (char c : Nl) N *= ext_of(c);
+  for (char c : Kl) K *= ext_of(c);
+  if (Bt == 0 || M == 0 || N == 0) return;
+  if (K == 0) return;
+
+  // operand A: [bat][M][K]
+  const double* Ap = A.base;
+  int64_t sAb, sAm, sAk;
+  double* Apack = nullptr;
+  if (!(collapse(bat, ea, sAb) && collapse(Ml, ea, sAm) && collapse(Kl, ea, sAk))) {
+    Apack = tmp_alloc(Bt * M * K);
+    Strided sp;
+    std::vector<char> order = bat;
+    order.insert(order.end(), Ml.begin(), Ml.end());
+    order.insert(order.end(), Kl.begin(), Kl.end());
+    sp.ndim = (int)order.size();
+    int64_t st = 1;
+    for (int d = sp.ndim - 1; d >= 0; --d) {
+      sp.ext[d] = ea[order[d]].first;
+      sp.s1[d] = ea[order[d]].second;
+      sp.s0[d] = st;
+      st *= sp.ext[d];
+    }
+    launch_copy_strided(Apack, A.base, sp, st_);
+    stats.packs++;
+    Ap = Apack;
+    sAb = M * K;
+    sAm = K;
+    sAk = 1;
+  }
+  const double* Bp = B.base;
+  int64_t sBb, sBn, sBk;
+  double* Bpack = nullptr;
+  if (!(collapse(bat, eb, sBb) && collapse(Nl, eb, sBn) && collapse(Kl, eb, sBk))) {
+    Bpack = tmp_alloc(Bt * N * K);
+    Strided sp;
+    std::vector<char> order = bat;
+    order.insert(order.end(), Nl.begin(), Nl.end());
+    order.insert(order.end(), Kl.begin(), Kl.end());
+    sp.ndim = (int)order.size();
+    int64_t st = 1;
+    for (int d = sp.ndim - 1; d >= 0; --d) {
+      sp.ext[d] = eb[order[d]].first;
+      sp.s1[d] = eb[order[d]].second;
+      sp.s0[d] = st;
+      st *= sp.ext[d];
+    }
+    launch_copy_strided(Bpack, B.base, sp, st_);
+    stats.packs++;
+    Bp = Bpack;
+    sBb = N * K;
+    sBn = K;
+    sBk = 1;
+  }
+  int64_t sCb, sCm, sCn;
+  bool cdirect = collapse(bat, eo, sCb) && collapse(Ml, eo, sCm) && collapse(Nl, eo, sCn);
+  double* Ctmp = nullptr;
+  double* Cp = O.base;
+  double alpha = op.alpha, beta = 1.0;
+  if (!cdirect) {
+    Ctmp = tmp_alloc(Bt * M * N);
+    Cp = Ctmp;
+    sCb = M * N;
+    sCm = N;
+    sCn = 1;
+    alpha = 1.0;
+    beta = 0.0;
+  }
+  if (Bt > 65535 || M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) throw std::runtime_error("GEMM too large");
+  double flops = 2.0 * (double)Bt * M * N * K;
+  bool done = false;
+  if (prec_ == PREC_MIXED && flops >= tc_min_flops) {
+    bool b_const = (g_.T[op.b.t].role == ROLE_INPUT_H) && (Bpack == nullptr);
+    (void)b_const;
+    done = tc_contract((int)Bt, (int)M, (int)N, (int)K, Ap, sAb, sAm, sAk, Bp, sBb, sBn, sBk, Cp, sCb, sCm, sCn,
+                       alpha, false);
+    if (!cdirect && !done) {
+      // tc path writes C = alpha*AB + C; Ctmp must be zero for beta = 0 semantics
+    }
+    if (done) {
+      stats.tc_calls++;
+      stats.tc_flops += flops;
+    }
+  }
+  if (!done) {
+    if (!cdirect) {
+      // plain GEMM overwrites Ctmp (beta = 0)
+    }
+    GemmArgs ga;
+    ga.batch = (int)Bt;
+    ga.M = (int)M;
+    ga.N = (int)N;
+    ga.K = (int)K;
+    ga.A = Ap;
+    ga.sAb = sAb;
+    ga.sAm = sAm;
+    ga.sAk = sAk;
+    ga.B = Bp;
+    ga.sBb = sBb;
+    ga.sBn = sBn;
+    ga.sBk = sBk;
+    ga.C = Cp;
+    ga.sCb = sCb;
+    ga.sCm = sCm;
+    ga.sCn = sCn;
+    ga.alpha = alpha;
+    ga.beta = beta;
+    launch_dgemm(ga, st_);
+    stats.gemm_calls++;
+    stats.gemm_flops += flops;
+  }
+  if (!cdirect) {
+    Strided sp;
+    std::vector<char> order = bat;
+    order.insert(order.end(), Ml.begin(), Ml.end());
+    order.insert(order.end(), Nl.begin(), Nl.end());
+    sp.ndim = (int)order.size();
+    int64_t st = 1;
+    for (int d = sp.ndim - 1; d >= 0; --d) {
+      sp.ext[d] = eo[order[d]].first;
+      sp.s0[d] = eo[order[d]].second;
+      sp.s1[d] = st;
+      st *= sp.ext[d];
+    }
+    launch_axpy_strided(O.base, Ctmp, sp, op.alpha, st_);
+    stats.scatters++;
+  }
+  if (Apack) tmp_free(Apack);
+  if (Bpack) tmp_free(Bpack);
+  if (Ctmp) tmp_free(Ctmp);
+}
+
+void Executor::exec_axpy(const Op& op) {
+  SView O = resolve(op.out), A = resolve(op.a);
+  auto lo = merge(O, op.lo), la = merge(A, op.la);
+  if (lo.size() != la.size()) throw std::runtime_error("axpy label sets differ");
+  Strided sp;
+  sp.ndim = (int)lo.size();
+  for (int d = 0; d < sp.ndim; ++d) {
+    sp.ext[d] = lo[d].e;
+    sp.s0[d] = lo[d].s;
+    bool found = false;
+    for (auto& l : la)
+      if (l.c == lo[d].c) {
+        if (l.e != lo[d].e) throw std::runtime_error("axpy extent mismatch");
+        sp.s1[d] = l.s;
+        found = true;
+      }
+    if (!found) throw std::runtime_error("axpy label sets differ");
+  }
+  if (sp.ndim == 0) {
+    sp.ndim = 1;
+    sp.ext[0] = 1;
+    sp.s0[0] = sp.s1[0] = 0;
+  }
+  launch_axpy_strided(O.base, A.base, sp, op.alpha, st_);
+  stats.axpys++;
+}
+
+void Executor::run(const Prog& p) {
+  // live ranges of temporaries owned by this run
+  std::map<int, int> first_write, last_use;
+  for (int i = 0; i < (int)p.size(); ++i) {
+    const Op& op = p[i];
+    if (!first_write.count(op.out.t)) first_write[op.out.t] = i;
+    last_use[op.out.t] = i;
+    last_use[op.a.t] = i;
+    if (op.kind == 'C') last_use[op.b.t] = i;
+  }
+  std::set<int> run_temps;
+  for (auto& kv : first_write) {
+    int t = kv.first;
+    const TS& s = ts_[t];
+    if (!s.p) run_temps.insert(t);
+  }
+  for (int i = 0; i < (int)p.size(); ++i) {
+    const Op& op = p[i];
+    auto check_read = [&](int t) {
+      if (!ts_[t].p) throw std::runtime_error("read before write: " + g_.T[t].name);
+    };
+    check_read(op.a.t);
+    if (op.kind == 'C') check_read(op.b.t);
+    if (first_write[op.out.t] == i) {
+      int t = op.out.t;
+      if (run_temps.count(t)) {
+        ts_[t].p = tmp_alloc(numel(t));
+        ts_[t].owned = false;
+        ts_[t].zstride = -1;
+      }
+      zero_tensor(t);
+    }
+    if (op.kind == 'C')
+      exec_contract(op);
+    else
+      exec_axpy(op);
+    // release temporaries whose last use was this op
+    auto release = [&](int t) {
+      if (run_temps.count(t) && last_use[t] == i && ts_[t].p) {
+        tmp_free(ts_[t].p);
+        ts_[t].p = nullptr;
+      }
+    };
+    release(op.out.t);
+    release(op.a.t);
+    if (op.kind == 'C') release(op.b.t);
+  }
+  CK(cudaGetLastError());
+}
+
+}  // namespace ccsd

@@ -1,0 +1,107 @@
+// Executes tensor programs on one GPU stream.
+//
+// Each contraction out[lo] += alpha * sum a[la] b[lb] is mapped onto one
+// batched GEMM: labels shared by a, b and out are the batch, labels of a and
+// out the M extent, of b and out the N extent, of a and b the K extent.
+// Operands whose memory already has that shape are addressed in place;
+// others are gathered into a contiguous buffer first.  Temporaries of a
+// program run are allocated and freed stream-ordered around their live range.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "ir.h"
+#include "kernels.cuh"
+
+namespace ccsd {
+
+enum Precision : int { PREC_FP64 = 0, PREC_MIXED = 1 };
+
+struct ExecStats {
+  int64_t gemm_calls = 0, tc_calls = 0, packs = 0, scatters = 0, axpys = 0;
+  double gemm_flops = 0.0, tc_flops = 0.0;
+};
+
+class Executor {
+ public:
+  Executor(const Graph& g, int o, int v, int naux, int nvec_max, cudaStream_t st);
+  ~Executor();
+  Executor(const Executor&) = delete;
+  Executor& operator=(const Executor&) = delete;
+
+  void set_nvec(int nvec);
+  int nvec() const { return nvec_; }
+  // bind an external device buffer; zstride is the distance between vector slices
+  // of a tensor whose leading class is 'z' (-1: contiguous)
+  void bind(int t, double* p, int64_t zstride = -1);
+  void unbind(int t);
+  // allocate an owned buffer that persists across program runs
+  void alloc_persistent(int t);
+  double* ptr(int t) const { return ts_[t].p; }
+  int64_t numel(int t) const;  // with the current nvec
+  void run(const Prog& p);
+
+  void set_precision(int prec, int splits) {
+    prec_ = prec;
+    splits_ = splits;
+  }
+  int precision() const { return prec_; }
+  // contractions with fewer flops than this stay on the FP64 path in mixed mode
+  double tc_min_flops = 2.0e9;
+  ExecStats stats;
+  cudaStream_t stream() const { return st_; }
+  // device scratch for reductions
+  double* scratch(int64_t n);
+  // size of the largest bf16 operand cache entry, for tests
+  size_t cache_bytes() const { return cache_bytes_; }
+  void clear_cache();
+
+ private:
+  struct TS {
+    double* p = nullptr;
+    bool owned = false;
+    bool bound = false;
+    int64_t zstride = -1;
+  };
+  struct SView {
+    double* base;
+    int nd;
+    int64_t ext[kMaxDims], str[kMaxDims];
+  };
+  struct Lab {
+    char c;
+    int64_t e, s;
+  };
+  SView resolve(const Ref& r) const;
+  int64_t extent(char cls) const;
+  std::vector<Lab> merge(const SView& v, const std::string& lab) const;
+  void zero_tensor(int t);
+  void exec_contract(const Op& op);
+  void exec_axpy(const Op& op);
+  double* tmp_alloc(int64_t n);
+  void tmp_free(double* p);
+
+  const Graph& g_;
+  int o_, v_, naux_, nvec_max_, nvec_;
+  cudaStream_t st_;
+  std::vector<TS> ts_;
+  int prec_ = PREC_FP64, splits_ = 3;
+  double* scratch_ = nullptr;
+  int64_t scratch_n_ = 0;
+  size_t cache_bytes_ = 0;
+
+ public:
+  // tensor-core path (tc_gemm.cu); returns false when the op is not eligible
+  bool tc_contract(int batch, int M, int N, int K, const double* A, int64_t sAb, int64_t sAm, int64_t sAk,
+                   const double* B, int64_t sBb, int64_t sBn, int64_t sBk, double* C, int64_t sCb, int64_t sCm,
+                   int64_t sCn, double alpha, bool b_const);
+  struct CacheEntry;
+  std::vector<CacheEntry*> cache_;
+};
+
+}  // namespace ccsd

@@ -1,0 +1,488 @@
+// FP64 kernels: strided permute/accumulate, batched DFMA GEMM, amplitude-vector
+// operations (packed inner products, preconditioner, pair symmetrisation).
+#include "kernels.cuh"
+
+#include <algorithm>
+#include <stdexcept>
+
+namespace ccsd {
+
+static inline int grid_for(int64_t n, int block = 256, int cap = 152 * 16) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+// ---------------------------------------------------------------------------
+// strided axpy / zero
+// ---------------------------------------------------------------------------
+template <typename I, bool COPY>
+__global__ void k_axpy_strided(double* __restrict__ dst, const double* __restrict__ src, Strided sp, I total,
+                               double alpha) {
+  for (I idx = (I)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (I)gridDim.x * blockDim.x) {
+    I r = idx;
+    int64_t o0 = 0, o1 = 0;
+    for (int d = sp.ndim - 1; d >= 0; --d) {
+      I e = (I)sp.ext[d];
+      I c = r % e;
+      r /= e;
+      o0 += (int64_t)c * sp.s0[d];
+      o1 += (int64_t)c * sp.s1[d];
+    }
+    if (COPY)
+      dst[o0] = src[o1];
+    else
+      dst[o0] += alpha * src[o1];
+  }
+}
+
+template <typename I>
+__global__ void k_zero_strided(double* __restrict__ dst, Strided sp, I total) {
+  for (I idx = (I)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (I)gridDim.x * blockDim.x) {
+    I r = idx;
+    int64_t o0 = 0;
+    for (int d = sp.ndim - 1; d >= 0; --d) {
+      I e = (I)sp.ext[d];
+      I c = r % e;
+      r /= e;
+      o0 += (int64_t)c * sp.s0[d];
+    }
+    dst[o0] = 0.0;
+  }
+}
+
+void launch_axpy_strided(double* dst, const double* src, const Strided& sp, double alpha, cudaStream_t st) {
+  int64_t n = sp.total();
+  if (n == 0) return;
+  if (n < (int64_t(1) << 31))
+    k_axpy_strided<uint32_t, false><<<grid_for(n), 256, 0, st>>>(dst, src, sp, (uint32_t)n, alpha);
+  else
+    k_axpy_strided<uint64_t, false><<<grid_for(n), 256, 0, st>>>(dst, src, sp, (uint64_t)n, alpha);
+}
+
+void launch_copy_strided(double* dst, const double* src, const Strided& sp, cudaStream_t st) {
+  int64_t n = sp.total();
+  if (n == 0) return;
+  if (n < (int64_t(1) << 31))
+    k_axpy_strided<uint32_t, true><<<grid_for(n), 256, 0, st>>>(dst, src, sp, (uint32_t)n, 1.0);
+  else
+    k_axpy_strided<uint64_t, true><<<grid_for(n), 256, 0, st>>>(dst, src, sp, (uint64_t)n, 1.0);
+}
+
+void launch_zero_strided(double* dst, const Strided& sp, cudaStream_t st) {
+  int64_t n = sp.total();
+  if (n == 0) return;
+  if (n < (int64_t(1) << 31))
+    k_zero_strided<uint32_t><<<grid_for(n), 256, 0, st>>>(dst, sp, (uint32_t)n);
+  else
+    k_zero_strided<uint64_t><<<grid_for(n), 256, 0, st>>>(dst, sp, (uint64_t)n);
+}
+
+// ---------------------------------------------------------------------------
+// batched FP64 GEMM, 64x64 tiles, 16-deep k steps, 4x4 outputs per thread
+// ---------------------------------------------------------------------------
+constexpr int DT = 64, DK = 16;
+
+__global__ void __launch_bounds__(256) k_dgemm(GemmArgs g) {
+  __shared__ double As[DK][DT + 1];
+  __shared__ double Bs[DK][DT + 1];
+  const int b = blockIdx.z;
+  const int m0 = blockIdx.y * DT, n0 = blockIdx.x * DT;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const double* A = g.A + (int64_t)b * g.sAb;
+  const double* B = g.B + (int64_t)b * g.sBb;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  const bool akfast = (g.sAk == 1);
+  const bool bkfast = (g.sBk == 1);
+  for (int k0 = 0; k0 < g.K; k0 += DK) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int e = tid + 256 * r;
+      int kk, mm;
+      if (akfast) {
+        kk = e & 15;
+        mm = e >> 4;
+      } else {
+        mm = e & 63;
+        kk = e >> 6;
+      }
+      int m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < g.M && k < g.K) ? A[(int64_t)m * g.sAm + (int64_t)k * g.sAk] : 0.0;
+      int nn;
+      if (bkfast) {
+        kk = e & 15;
+        nn = e >> 4;
+      } else {
+        nn = e & 63;
+        kk = e >> 6;
+      }
+      int n = n0 + nn;
+      k = k0 + kk;
+      Bs[kk][nn] = (n < g.N && k < g.K) ? B[(int64_t)n * g.sBn + (int64_t)k * g.sBk] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < DK; ++kk) {
+      double a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  double* C = g.C + (int64_t)b * g.sCb;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int m = m0 + ty + 16 * i;
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int n = n0 + tx + 16 * j;
+      if (n >= g.N) continue;
+      double* c = C + (int64_t)m * g.sCm + (int64_t)n * g.sCn;
+      double val = g.alpha * acc[i][j];
+      if (g.beta != 0.0) val += g.beta * (*c);
+      *c = val;
+    }
+  }
+}
+
+void launch_dgemm(const GemmArgs& g, cudaStream_t st) {
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
+  if (g.K <= 0) throw std::runtime_error("dgemm: K must be positive");
+  if (g.batch > 65535) throw std::runtime_error("dgemm: batch too large");
+  dim3 grid((g.N + DT - 1) / DT, (g.M + DT - 1) / DT, g.batch);
+  if (grid.y > 65535) throw std::runtime_error("dgemm: M too large");
+  k_dgemm<<<grid, 256, 0, st>>>(g);
+}
+
+// ---------------------------------------------------------------------------
+// amplitude vectors
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double pair_weight(const VecShape& s, int64_t k) {
+  // k indexes the whole vector; singles weigh 1
+  int64_t n1 = s.n1();
+  if (k < n1) return 1.0;
+  uint32_t kd = (uint32_t)(k - n1);
+  uint32_t v = (uint32_t)s.v, o = (uint32_t)s.o;
+  uint32_t b = kd % v;
+  kd /= v;
+  uint32_t a = kd % v;
+  kd /= v;
+  uint32_t j = kd % o;
+  uint32_t i = kd / o;
+  return (i == j && a == b) ? 1.0 : 0.5;
+}
+
+constexpr int TP = 8, TQ = 8, WD_BLOCK = 256;
+
+__global__ void __launch_bounds__(WD_BLOCK) k_wdot_partial(VecShape s, const double* __restrict__ X, int64_t ldx,
+                                                           int np, const double* __restrict__ Y, int64_t ldy, int nq,
+                                                           double* __restrict__ work) {
+  const int p0 = blockIdx.y * TP, q0 = blockIdx.z * TQ;
+  const int pn = min(TP, np - p0), qn = min(TQ, nq - q0);
+  double acc[TP][TQ];
+#pragma unroll
+  for (int p = 0; p < TP; ++p)
+#pragma unroll
+    for (int q = 0; q < TQ; ++q) acc[p][q] = 0.0;
+  const int64_t dim = s.dim();
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < dim; k += (int64_t)gridDim.x * blockDim.x) {
+    double w = pair_weight(s, k);
+    double yv[TQ];
+#pragma unroll
+    for (int q = 0; q < TQ; ++q) yv[q] = (q < qn) ? w * Y[(int64_t)(q0 + q) * ldy + k] : 0.0;
+#pragma unroll
+    for (int p = 0; p < TP; ++p) {
+      double xv = (p < pn) ? X[(int64_t)(p0 + p) * ldx + k] : 0.0;
+#pragma unroll
+      for (int q = 0; q < TQ; ++q) acc[p][q] = fma(xv, yv[q], acc[p][q]);
+    }
+  }
+  __shared__ double red[WD_BLOCK / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int p = 0; p < pn; ++p) {
+    for (int q = 0; q < qn; ++q) {
+      double vsum = acc[p][q];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) vsum += __shfl_down_sync(0xffffffffu, vsum, off);
+      if (lane == 0) red[warp] = vsum;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double tsum = 0.0;
+        for (int w2 = 0; w2 < WD_BLOCK / 32; ++w2) tsum += red[w2];
+        work[((int64_t)blockIdx.x * np + (p0 + p)) * nq + (q0 + q)] = tsum;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void k_wdot_final(int nchunks, int np, int nq, const double* __restrict__ work, double* G, int ldg) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= np * nq) return;
+  int p = idx / nq, q = idx % nq;
+  double s = 0.0;
+  for (int c = 0; c < nchunks; ++c) s += work[((int64_t)c * np + p) * nq + q];
+  G[p * ldg + q] = s;
+}
+
+static int wdot_chunks() { return 152 * 2; }
+
+int64_t wdot_work_size(int np, int nq) { return (int64_t)wdot_chunks() * np * nq; }
+
+void launch_wdot(const VecShape& s, const double* X, int64_t ldx, int np, const double* Y, int64_t ldy, int nq,
+                 double* G, int ldg, double* work, cudaStream_t st) {
+  if (np <= 0 || nq <= 0) return;
+  int nch = wdot_chunks();
+  dim3 grid(nch, (np + TP - 1) / TP, (nq + TQ - 1) / TQ);
+  k_wdot_partial<<<grid, WD_BLOCK, 0, st>>>(s, X, ldx, np, Y, ldy, nq, work);
+  k_wdot_final<<<(np * nq + 127) / 128, 128, 0, st>>>(nch, np, nq, work, G, ldg);
+}
+
+__global__ void k_lincomb(int64_t dim, const double* __restrict__ X, int64_t ldx, int np, const double* __restrict__ c,
+                          int ldc, double* __restrict__ Y, int64_t ldy, int nq, bool accumulate) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < dim; k += (int64_t)gridDim.x * blockDim.x) {
+    for (int q0 = 0; q0 < nq; q0 += 8) {
+      double acc[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+      for (int p = 0; p < np; ++p) {
+        double xv = X[(int64_t)p * ldx + k];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q0 + q < nq) acc[q] = fma(c[p * ldc + q0 + q], xv, acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (q0 + q >= nq) break;
+        double* y = Y + (int64_t)(q0 + q) * ldy + k;
+        *y = accumulate ? (*y + acc[q]) : acc[q];
+      }
+    }
+  }
+}
+
+void launch_lincomb(const VecShape& s, const double* X, int64_t ldx, int np, const double* c, int ldc, double* Y,
+                    int64_t ldy, int nq, bool accumulate, cudaStream_t st) {
+  int64_t dim = s.dim();
+  k_lincomb<<<grid_for(dim), 256, 0, st>>>(dim, X, ldx, np, c, ldc, Y, ldy, nq, accumulate);
+}
+
+__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    y[k] = a * x[k] + (b == 0.0 ? 0.0 : b * y[k]);
+}
+
+void launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st) {
+  if (n > 0) k_axpby<<<grid_for(n), 256, 0, st>>>(n, a, x, b, y);
+}
+
+__global__ void k_precond(VecShape s, const double* __restrict__ eps, const double* __restrict__ x,
+                          double* __restrict__ y, double shift) {
+  const int64_t dim = s.dim(), n1 = s.n1();
+  const uint32_t o = s.o, v = s.v;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < dim; k += (int64_t)gridDim.x * blockDim.x) {
+    double d;
+    if (k < n1) {
+      uint32_t a = (uint32_t)k % v, i = (uint32_t)k / v;
+      d = eps[o + a] - eps[i];
+    } else {
+      uint32_t kd = (uint32_t)(k - n1);
+      uint32_t b = kd % v;
+      kd /= v;
+      uint32_t a = kd % v;
+      kd /= v;
+      uint32_t j = kd % o, i = kd / o;
+      d = eps[o + a] + eps[o + b] - eps[i] - eps[j];
+    }
+    y[k] = x[k] / (d - shift);
+  }
+}
+
+void launch_precond(const VecShape& s, const double* eps, const double* x, double* y, double shift,
+                    cudaStream_t st) {
+  k_precond<<<grid_for(s.dim()), 256, 0, st>>>(s, eps, x, y, shift);
+}
+
+__global__ void k_weight(VecShape s, const double* __restrict__ x, double* __restrict__ y, int nvec, int64_t ld) {
+  const int64_t dim = s.dim();
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < dim * nvec;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t vi = k / dim, e = k % dim;
+    y[vi * ld + e] = pair_weight(s, e) * x[vi * ld + e];
+  }
+}
+
+void launch_weight(const VecShape& s, const double* x, double* y, int nvec, int64_t ld, cudaStream_t st) {
+  k_weight<<<grid_for(s.dim() * nvec), 256, 0, st>>>(s, x, y, nvec, ld);
+}
+
+__global__ void k_packed_grad(VecShape s, const double* __restrict__ g, double* __restrict__ y, int nvec,
+                              int64_t ld) {
+  const int64_t dim = s.dim(), n1 = s.n1();
+  const uint32_t o = s.o, v = s.v;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < dim * nvec;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t vi = k / dim, e = k % dim;
+    const double* gv = g + vi * ld;
+    double r;
+    if (e < n1) {
+      r = gv[e];
+    } else {
+      uint32_t kd = (uint32_t)(e - n1);
+      uint32_t b = kd % v;
+      uint32_t t = kd / v;
+      uint32_t a = t % v;
+      t /= v;
+      uint32_t j = t % o, i = t / o;
+      if (i == j && a == b) {
+        r = gv[e];
+      } else {
+        int64_t tr = n1 + (((int64_t)j * o + i) * v + b) * v + a;
+        r = gv[e] + gv[tr];
+      }
+    }
+    y[vi * ld + e] = r;
+  }
+}
+
+void launch_packed_grad(const VecShape& s, const double* g, double* y, int nvec, int64_t ld, cudaStream_t st) {
+  if (g == y) throw std::runtime_error("packed_grad must be out of place");
+  k_packed_grad<<<grid_for(s.dim() * nvec), 256, 0, st>>>(s, g, y, nvec, ld);
+}
+
+__global__ void k_maxabs_partial(int64_t n, const double* __restrict__ x, double* work, int with_index) {
+  double best = -1.0;
+  int64_t bi = 0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double a = fabs(x[k]);
+    if (a > best) {
+      best = a;
+      bi = k;
+    }
+  }
+  __shared__ double sb[256];
+  __shared__ int64_t si[256];
+  sb[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) {
+      double ob = sb[threadIdx.x + off];
+      int64_t oi = si[threadIdx.x + off];
+      if (ob > sb[threadIdx.x] || (ob == sb[threadIdx.x] && oi < si[threadIdx.x])) {
+        sb[threadIdx.x] = ob;
+        si[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    work[2 * blockIdx.x] = sb[0];
+    work[2 * blockIdx.x + 1] = (double)si[0];
+  }
+}
+
+__global__ void k_maxabs_final(int nb, const double* work, const double* x, double* out, int with_index) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double best = -1.0, bi = 0.0;
+  for (int b = 0; b < nb; ++b) {
+    double v = work[2 * b], i = work[2 * b + 1];
+    if (v > best || (v == best && i < bi)) {
+      best = v;
+      bi = i;
+    }
+  }
+  if (with_index) {
+    out[0] = bi;
+    out[1] = x[(int64_t)bi];
+  } else {
+    out[0] = best;
+  }
+}
+
+void launch_maxabs(int64_t n, const double* x, double* out, double* work, cudaStream_t st) {
+  int nb = 256;
+  k_maxabs_partial<<<nb, 256, 0, st>>>(n, x, work, 0);
+  k_maxabs_final<<<1, 32, 0, st>>>(nb, work, x, out, 0);
+}
+
+void launch_argmaxabs(int64_t n, const double* x, double* out, double* work, cudaStream_t st) {
+  int nb = 256;
+  k_maxabs_partial<<<nb, 256, 0, st>>>(n, x, work, 1);
+  k_maxabs_final<<<1, 32, 0, st>>>(nb, work, x, out, 1);
+}
+
+__global__ void k_dot_partial(int64_t n, const double* __restrict__ x, const double* __restrict__ y, double* work) {
+  double s = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    s = fma(x[k], y[k], s);
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) work[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_final(int nb, const double* work, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += work[b];
+  out[0] = s;
+}
+
+void launch_dot(int64_t n, const double* x, const double* y, double* out, double* work, cudaStream_t st) {
+  int nb = 512;
+  k_dot_partial<<<nb, 256, 0, st>>>(n, x, y, work);
+  k_sum_final<<<1, 32, 0, st>>>(nb, work, out);
+}
+
+// <L|tau_sigma|(r0 + R)>: singles y[j,b] = r0 L1[j,b] + sum_ia (1 + delta_ia,jb) L2[i,j,a,b] R1[i,a];
+// doubles y2 = r0 L2.  (A single tau_jb on R1 gives a double; only <L2| sees it.)
+__global__ void k_tau_singles(VecShape s, double r0, const double* __restrict__ L, const double* __restrict__ R,
+                              double* __restrict__ y) {
+  const int o = s.o, v = s.v;
+  const int jb = blockIdx.x;
+  const int j = jb / v, b = jb % v;
+  const int64_t n1 = s.n1();
+  const double* L2 = L + n1;
+  double acc = 0.0;
+  for (int ia = threadIdx.x; ia < o * v; ia += blockDim.x) {
+    int i = ia / v, a = ia % v;
+    double l = L2[(((int64_t)i * o + j) * v + a) * v + b];
+    double f = (i == j && a == b) ? 2.0 : 1.0;
+    acc = fma(f * l, R[ia], acc);
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) y[jb] = r0 * L[jb] + sh[0];
+}
+
+void launch_tau_expectation(const VecShape& s, double r0, const double* L, const double* R, double* y,
+                            cudaStream_t st) {
+  k_tau_singles<<<s.o * s.v, 256, 0, st>>>(s, r0, L, R, y);
+  int64_t n2 = s.dim() - s.n1();
+  k_axpby<<<grid_for(n2), 256, 0, st>>>(n2, r0, L + s.n1(), 0.0, y + s.n1());
+}
+
+}  // namespace ccsd
