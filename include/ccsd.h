@@ -111,6 +111,13 @@ ccsd_status ccsd_jacobian_transform(ccsd_handle h, int side, int nvec, const dou
  * omega[dim] output; e may be NULL. */
 ccsd_status ccsd_residual(ccsd_handle h, const double* t, double* omega, double* e);
 
+/* Restore amplitudes (checkpoint / warm start): t[dim] becomes the ground-state
+ * amplitude vector used by the transforms and couplings, as if ccsd_solve_ground
+ * had converged to it; lambda[dim] (may be NULL) restores the ground
+ * multipliers, otherwise they are solved for.  Returns the energy at t in *e
+ * (may be NULL).  Invalidates EOM states.  No convergence check is made on t. */
+ccsd_status ccsd_set_amplitudes(ccsd_handle h, const double* t, const double* lambda, double* e);
+
 /* Copy out the converged amplitudes t[dim], the ground multipliers lambda[dim],
  * and EOM states right[k][dim] / left[k][dim] (NULL pointers are skipped). */
 ccsd_status ccsd_get_amplitudes(ccsd_handle h, double* t, double* lambda);

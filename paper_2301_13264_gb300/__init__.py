@@ -16,6 +16,7 @@ from .binding import (  # noqa: F401
     ccsd_get_states,
     ccsd_jacobian_transform,
     ccsd_residual,
+    ccsd_set_amplitudes,
     ccsd_solve_ground,
     ccsd_stats,
     eom_solve_left,

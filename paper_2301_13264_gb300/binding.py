@@ -65,6 +65,7 @@ def lib():
         L.ccsd_jacobian_transform.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
         L.ccsd_residual.argtypes = [_P, _P, _P, _D]
         L.ccsd_get_amplitudes.argtypes = [_P, _P, _P]
+        L.ccsd_set_amplitudes.argtypes = [_P, _P, _P, _D]
         L.ccsd_get_states.argtypes = [_P, ctypes.c_int, _D, _P, _P]
         L.ccsd_coupling_densities.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
         L.ccsd_derivative_coupling.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _D]
@@ -78,7 +79,7 @@ def lib():
         L.ccsd_describe_program.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_size_t]
         L.ccsd_describe_program.restype = ctypes.c_longlong
         for name in ("ccsd_create", "ccsd_solve_ground", "eom_solve_right", "eom_solve_left",
-                     "ccsd_jacobian_transform", "ccsd_residual", "ccsd_get_amplitudes", "ccsd_get_states",
+                     "ccsd_jacobian_transform", "ccsd_residual", "ccsd_get_amplitudes", "ccsd_set_amplitudes", "ccsd_get_states",
                      "ccsd_coupling_densities", "ccsd_derivative_coupling", "ccsd_stats"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
@@ -152,6 +153,12 @@ def ccsd_jacobian_transform(h, side, nvec, x, y):
 def ccsd_residual(h, t, omega):
     e = ctypes.c_double()
     _check(h, lib().ccsd_residual(h, _ptr(t), _ptr(omega), ctypes.byref(e)))
+    return e.value
+
+
+def ccsd_set_amplitudes(h, t, lam=None):
+    e = ctypes.c_double()
+    _check(h, lib().ccsd_set_amplitudes(h, _ptr(t), _ptr(lam), ctypes.byref(e)))
     return e.value
 
 

@@ -782,6 +782,32 @@ ccsd_status ccsd_jacobian_transform(ccsd_handle c, int side, int nvec, const dou
   });
 }
 
+ccsd_status ccsd_set_amplitudes(ccsd_handle c, const double* t, const double* lambda, double* e) {
+  return guarded(c, [&] {
+    if (!t) throw Err(CCSD_ERR_ARG, "null amplitudes");
+    const int64_t dim = c->dim;
+    CUDA_OK(cudaMemcpyAsync(c->t.p, t, dim * sizeof(double), cudaMemcpyDefault, c->st));
+    c->have_ground = c->have_right = c->have_left = false;
+    c->dens_k = c->dens_l = -1;
+    DevBuf om(dim);
+    double en = forward(c, c->t.p, om.p);
+    c->e_ccsd = en;
+    c->have_ground = true;
+    DevBuf zero(dim);
+    CUDA_OK(cudaMemsetAsync(zero.p, 0, dim * sizeof(double), c->st));
+    left_block(c, zero.p, c->eta.p, 1, 1.0);
+    if (lambda) {
+      CUDA_OK(cudaMemcpyAsync(c->lam.p, lambda, dim * sizeof(double), cudaMemcpyDefault, c->st));
+    } else {
+      launch_precond(c->vs, c->eps.p, c->eta.p, c->lam.p, 0.0, c->st);
+      launch_axpby(dim, 0.0, c->lam.p, -1.0, c->lam.p, c->st);
+      solve_left_linear(c, c->eta.p, c->lam.p, c->opt.tol_lin);
+    }
+    sync(c);
+    if (e) *e = en;
+  });
+}
+
 ccsd_status ccsd_get_amplitudes(ccsd_handle c, double* t, double* lambda) {
   return guarded(c, [&] {
     if (!c->have_ground) throw Err(CCSD_ERR_STATE, "ground state not solved");

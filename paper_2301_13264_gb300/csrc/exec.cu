@@ -3,6 +3,8 @@
 
 #include <algorithm>
 #include <map>
+#include <cstdio>
+#include <cstdlib>
 #include <stdexcept>
 
 namespace ccsd {
@@ -405,8 +407,20 @@ void Executor::run(const Prog& p) {
     const TS& s = ts_[t];
     if (!s.p) run_temps.insert(t);
   }
+  // CCSD_OP_TIMING=1: time every op with events on the stream and print one line per op
+  static const bool op_timing = [] {
+    const char* e = getenv("CCSD_OP_TIMING");
+    return e && e[0] == '1';
+  }();
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (op_timing) {
+    CK(cudaEventCreate(&ev0));
+    CK(cudaEventCreate(&ev1));
+  }
   for (int i = 0; i < (int)p.size(); ++i) {
     const Op& op = p[i];
+    if (op_timing) CK(cudaEventRecord(ev0, st_));
+    double f0 = stats.gemm_flops + stats.tc_flops;
     auto check_read = [&](int t) {
       if (!ts_[t].p) throw std::runtime_error("read before write: " + g_.T[t].name);
     };
@@ -425,6 +439,17 @@ void Executor::run(const Prog& p) {
       exec_contract(op);
     else
       exec_axpy(op);
+    if (op_timing) {
+      CK(cudaEventRecord(ev1, st_));
+      CK(cudaEventSynchronize(ev1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ev0, ev1));
+      double fl = stats.gemm_flops + stats.tc_flops - f0;
+      fprintf(stderr, "[op %3d] %c %-14s %-8s <- %-14s %-8s %-14s %-8s %9.3f ms %10.3f GF/s\n", i, op.kind,
+              g_.T[op.out.t].name.c_str(), op.lo.c_str(), g_.T[op.a.t].name.c_str(), op.la.c_str(),
+              op.kind == 'C' ? g_.T[op.b.t].name.c_str() : "", op.kind == 'C' ? op.lb.c_str() : "", ms,
+              ms > 0 ? fl / (ms * 1e6) : 0.0);
+    }
     // release temporaries whose last use was this op
     auto release = [&](int t) {
       if (run_temps.count(t) && last_use[t] == i && ts_[t].p) {
@@ -435,6 +460,10 @@ void Executor::run(const Prog& p) {
     release(op.out.t);
     release(op.a.t);
     if (op.kind == 'C') release(op.b.t);
+  }
+  if (op_timing) {
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
   }
   CK(cudaGetLastError());
 }

@@ -84,10 +84,15 @@ void launch_zero_strided(double* dst, const Strided& sp, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 constexpr int DT = 64, DK = 16;
 
-__global__ void __launch_bounds__(256) k_dgemm(GemmArgs g) {
+// nsplit > 1: blockIdx.z = batch * nsplit + split; each split covers a K range and
+// writes alpha * partial sum to part[split][b][m][n] (C is not touched).
+__global__ void __launch_bounds__(256) k_dgemm(GemmArgs g, int nsplit, int kchunk, double* part) {
   __shared__ double As[DK][DT + 1];
   __shared__ double Bs[DK][DT + 1];
-  const int b = blockIdx.z;
+  const int b = blockIdx.z / nsplit;
+  const int split = blockIdx.z % nsplit;
+  const int kbeg = split * kchunk;
+  const int kend = min(g.K, kbeg + kchunk);
   const int m0 = blockIdx.y * DT, n0 = blockIdx.x * DT;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(256) k_dgemm(GemmArgs g) {
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
   const bool akfast = (g.sAk == 1);
   const bool bkfast = (g.sBk == 1);
-  for (int k0 = 0; k0 < g.K; k0 += DK) {
+  for (int k0 = kbeg; k0 < kend; k0 += DK) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       int e = tid + 256 * r;
@@ -113,7 +118,7 @@ __global__ void __launch_bounds__(256) k_dgemm(GemmArgs g) {
         kk = e >> 6;
       }
       int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < g.M && k < g.K) ? A[(int64_t)m * g.sAm + (int64_t)k * g.sAk] : 0.0;
+      As[kk][mm] = (m < g.M && k < kend) ? A[(int64_t)m * g.sAm + (int64_t)k * g.sAk] : 0.0;
       int nn;
       if (bkfast) {
         kk = e & 15;
@@ -124,7 +129,7 @@ __global__ void __launch_bounds__(256) k_dgemm(GemmArgs g) {
       }
       int n = n0 + nn;
       k = k0 + kk;
-      Bs[kk][nn] = (n < g.N && k < g.K) ? B[(int64_t)n * g.sBn + (int64_t)k * g.sBk] : 0.0;
+      Bs[kk][nn] = (n < g.N && k < kend) ? B[(int64_t)n * g.sBn + (int64_t)k * g.sBk] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -140,6 +145,20 @@ __global__ void __launch_bounds__(256) k_dgemm(GemmArgs g) {
         for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
     }
     __syncthreads();
+  }
+  if (nsplit > 1) {
+    double* P = part + ((int64_t)split * g.batch + b) * g.M * g.N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      int m = m0 + ty + 16 * i;
+      if (m >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int n = n0 + tx + 16 * j;
+        if (n < g.N) P[(int64_t)m * g.N + n] = g.alpha * acc[i][j];
+      }
+    }
+    return;
   }
   double* C = g.C + (int64_t)b * g.sCb;
 #pragma unroll
@@ -158,13 +177,86 @@ __global__ void __launch_bounds__(256) k_dgemm(GemmArgs g) {
   }
 }
 
+// Dot-product shapes (few outputs): one block per (split, output pair, batch).
+// part[split][b][m][n] = alpha * sum_{k in split} A[b][m][k] B[b][n][k]
+__global__ void __launch_bounds__(256) k_ddot_split(GemmArgs g, int nsplit, int64_t kchunk, double* part) {
+  const int split = blockIdx.x;
+  const int mn = blockIdx.y;
+  const int b = blockIdx.z;
+  const int m = mn / g.N, n = mn % g.N;
+  const double* A = g.A + (int64_t)b * g.sAb + (int64_t)m * g.sAm;
+  const double* B = g.B + (int64_t)b * g.sBb + (int64_t)n * g.sBn;
+  const int64_t kbeg = split * kchunk;
+  const int64_t kend = min((int64_t)g.K, kbeg + kchunk);
+  double s = 0.0;
+  for (int64_t k = kbeg + threadIdx.x; k < kend; k += blockDim.x) s = fma(A[k * g.sAk], B[k * g.sBk], s);
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[((int64_t)split * g.batch + b) * g.M * g.N + mn] = g.alpha * sh[0];
+}
+
+// C = sum_split part + beta * C
+__global__ void k_split_reduce(GemmArgs g, int nsplit, const double* __restrict__ part) {
+  const int64_t tot = (int64_t)g.batch * g.M * g.N;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = idx / ((int64_t)g.M * g.N);
+    int64_t r = idx % ((int64_t)g.M * g.N);
+    int64_t m = r / g.N, n = r % g.N;
+    double s = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) s += part[(int64_t)sp * tot + idx];
+    double* c = g.C + b * g.sCb + m * g.sCm + n * g.sCn;
+    *c = (g.beta != 0.0) ? s + g.beta * (*c) : s;
+  }
+}
+
 void launch_dgemm(const GemmArgs& g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
   if (g.K <= 0) throw std::runtime_error("dgemm: K must be positive");
   if (g.batch > 65535) throw std::runtime_error("dgemm: batch too large");
-  dim3 grid((g.N + DT - 1) / DT, (g.M + DT - 1) / DT, g.batch);
-  if (grid.y > 65535) throw std::runtime_error("dgemm: M too large");
-  k_dgemm<<<grid, 256, 0, st>>>(g);
+  const int target = 2 * 152;
+  const int64_t outputs = (int64_t)g.M * g.N;
+  if (outputs <= 64 && g.batch <= 64 && g.K >= 4096) {
+    int64_t nsplit = std::min<int64_t>(std::max<int64_t>(1, target / (outputs * g.batch)), (g.K + 2047) / 2048);
+    nsplit = std::max<int64_t>(nsplit, 1);
+    int64_t kchunk = (g.K + nsplit - 1) / nsplit;
+    double* part = nullptr;
+    size_t bytes = (size_t)nsplit * g.batch * outputs * sizeof(double);
+    if (cudaMallocAsync((void**)&part, bytes, st) != cudaSuccess) throw std::runtime_error("dgemm: workspace");
+    dim3 grid((unsigned)nsplit, (unsigned)outputs, g.batch);
+    k_ddot_split<<<grid, 256, 0, st>>>(g, (int)nsplit, kchunk, part);
+    k_split_reduce<<<grid_for(g.batch * outputs), 256, 0, st>>>(g, (int)nsplit, part);
+    cudaFreeAsync(part, st);
+    return;
+  }
+  const int64_t tm = (g.M + DT - 1) / DT, tn = (g.N + DT - 1) / DT;
+  const int64_t tiles = tm * tn * g.batch;
+  if (tm > 65535) throw std::runtime_error("dgemm: M too large");
+  int nsplit = 1;
+  if (tiles < target && g.K >= 8 * DK) {
+    nsplit = (int)std::min<int64_t>(target / tiles, g.K / (4 * DK));
+    nsplit = std::max(nsplit, 1);
+    while ((int64_t)g.batch * nsplit > 65535) --nsplit;
+  }
+  if (nsplit == 1) {
+    dim3 grid((unsigned)tn, (unsigned)tm, g.batch);
+    k_dgemm<<<grid, 256, 0, st>>>(g, 1, g.K, nullptr);
+    return;
+  }
+  int kchunk = (g.K + nsplit - 1) / nsplit;
+  kchunk = (kchunk + DK - 1) / DK * DK;
+  nsplit = (g.K + kchunk - 1) / kchunk;
+  double* part = nullptr;
+  size_t bytes = (size_t)nsplit * g.batch * g.M * g.N * sizeof(double);
+  if (cudaMallocAsync((void**)&part, bytes, st) != cudaSuccess) throw std::runtime_error("dgemm: workspace");
+  dim3 grid((unsigned)tn, (unsigned)tm, (unsigned)(g.batch * nsplit));
+  k_dgemm<<<grid, 256, 0, st>>>(g, nsplit, kchunk, part);
+  k_split_reduce<<<grid_for((int64_t)g.batch * g.M * g.N), 256, 0, st>>>(g, nsplit, part);
+  cudaFreeAsync(part, st);
 }
 
 // ---------------------------------------------------------------------------
