@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Throughput benchmark: EOM-CCSD Jacobian transformations per second.
+
+Workload: the thymine/aug-cc-pVDZ-shaped synthetic Hamiltonian (o=33, v=228,
+naux=900; seeded generator in paper_2301_13264_gb300.synth).  A step is one
+right (A X) and one left (X^T A) block transformation of `nvec` trial vectors
+at the converged ground-state amplitudes, i.e. 2*nvec Jacobian transforms.
+
+Prints one JSON line (rank 0).  For --gpus N > 1 (torchrun) each rank runs an
+independent replica on its own GPU (the path has no exchange step); the value
+is the total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Jacobian transforms/s and time-to-converged coupling at o=33,v=228 vs FP64 GPU form"
+UNIT = "transforms/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="thymine_adz")
+    ap.add_argument("--nvec", type=int, default=8)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--splits", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic flop count of one Jacobian transformation, from the program the
+# library runs (sum over contractions of 2 * product of label extents)
+# ---------------------------------------------------------------------------
+def transform_flops(o, v, naux, which="jvp"):
+    from paper_2301_13264_gb300 import binding as B
+    ext = {"o": o, "v": v, "n": o + v, "x": naux, "z": 1}
+    text = B.ccsd_describe_program(which)
+    cls = {}
+    total = 0.0
+    for line in text.splitlines():
+        f = line.split()
+        if f[0] == "T":
+            cls[int(f[1])] = "" if f[4] == "-" else f[4]
+        elif f[0] == "C":
+            labs = {}
+            for tid, blk, lab in ((int(f[1]), f[2], f[3]), (int(f[4]), f[5], f[6]), (int(f[7]), f[8], f[9])):
+                if lab == "-":
+                    continue
+                c = cls[tid]
+                for k, ch in enumerate(lab):
+                    b = blk[k]
+                    e = ext[b] if c[k] == "n" else ext[c[k]]
+                    labs[ch] = e
+            total += 2.0 * float(np.prod(list(labs.values())))
+    return total, None
+
+
+def ladder_flops_per_vector(o, v):
+    """Particle-particle ladder per vector, as the method counts it with the
+    pair-symmetric (+/-) packing: o^2 v^4 / 4 multiply-adds."""
+    return 2.0 * o * o * v ** 4 / 4.0
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-i", str(gpu_index), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle, as it stands, on the host cores
+# ---------------------------------------------------------------------------
+def oracle_sample(steps=1):
+    """Seconds per oracle right transform on the thymine/cc-pVDZ shape (o=33,
+    v=123, naux=550), the bounded sample of the transform workload."""
+    import torch
+    from oracle.solvers import System, Vec
+    from paper_2301_13264_gb300.synth import random_amplitudes, workload
+    H = workload("thymine_dz")
+    S = System(H.eps, H.h, H.B, H.o)
+    X1, X2 = random_amplitudes(H.o, H.v, 31, scale=0.01, nvec=2)
+    t = Vec(torch.as_tensor(X1[0]), torch.as_tensor(X2[0]))
+    r = Vec(torch.as_tensor(X1[1]), torch.as_tensor(X2[1]))
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        S.right(t, r)
+        times.append(time.perf_counter() - t0)
+    return times, H, torch.get_num_threads()
+
+
+def cpu_baseline_entry(o, v, naux):
+    times, Hs, threads = oracle_sample(1)
+    f_small, _ = transform_flops(Hs.o, Hs.v, Hs.naux)
+    f_full, _ = transform_flops(o, v, naux)
+    rate = (1.0 / times[-1]) * f_small / f_full
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"one oracle (numpy/torch FP64) right transform at o={Hs.o},v={Hs.v},naux={Hs.naux} took "
+                       f"{times[-1]:.1f} s; scaled to o={o},v={v},naux={naux} by the ratio of algorithmic flops "
+                       f"({f_small:.3g} / {f_full:.3g})")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2301_13264_gb300.synth import WORKLOADS
+    wl = WORKLOADS[args.workload]
+    o, v, naux = wl["o"], wl["v"], wl["naux"]
+    f_full, _ = transform_flops(o, v, naux)
+    for _ in range(args.warmup):
+        oracle_sample(1)
+    times = []
+    f_small = None
+    for _ in range(args.steps):
+        tt, Hs, threads = oracle_sample(1)
+        times.append(tt[-1])
+        if f_small is None:
+            f_small, _ = transform_flops(Hs.o, Hs.v, Hs.naux)
+    per = sum(times) / len(times)
+    value = (1.0 / per) * f_small / f_full
+    sample = (f"each step: one oracle right transform at o={Hs.o},v={Hs.v},naux={Hs.naux} ({per:.1f} s), scaled to "
+              f"o={o},v={v},naux={naux} by the algorithmic flop ratio")
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": f"{args.workload} o={o} v={v} naux={naux}", "side": "right"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2301_13264_gb300 import binding as B
+    from paper_2301_13264_gb300.synth import random_amplitudes, workload
+
+    torch.cuda.set_device(local_rank)
+    H = workload(args.workload)
+    o, v, naux = H.o, H.v, H.naux
+    dim = B.vector_dim(o, v)
+    stream = torch.cuda.Stream()
+    prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_FP64
+    opt = B.ccsd_default_options(precision=prec, splits=args.splits, stream=stream, tol_res=1e-7, tol_lin=1e-6,
+                                 max_iter=100)
+    h = B.ccsd_create(H.eps, H.h, H.B, o, v, naux, opt)
+    t_setup = time.perf_counter()
+    e_ccsd, iters = B.ccsd_solve_ground(h)
+    t_setup = time.perf_counter() - t_setup
+    X1, X2 = random_amplitudes(o, v, 1000 + rank, scale=0.01, nvec=args.nvec)
+    X = torch.as_tensor(np.concatenate([X1.reshape(args.nvec, -1), X2.reshape(args.nvec, -1)], axis=1),
+                        device="cuda").contiguous()
+    Y = torch.zeros_like(X)
+
+    def step():
+        B.ccsd_jacobian_transform(h, 0, args.nvec, X, Y)
+        B.ccsd_jacobian_transform(h, 1, args.nvec, X, Y)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    clocks = Clocks(vis.split(",")[local_rank] if vis and len(vis.split(",")) > local_rank else local_rank)
+    B.ccsd_profile_start(h)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    prof = B.ccsd_profile_stop(h)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    n_tr = 2 * args.nvec * args.steps * world
+    value = n_tr / (ms / 1e3)
+
+    # separate right/left rates (short extra runs, not part of the timed region)
+    def timed(side, reps=2):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            B.ccsd_jacobian_transform(h, side, args.nvec, X, Y)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return reps * args.nvec / (a.elapsed_time(b) / 1e3)
+
+    right_rate, left_rate = timed(0), timed(1)
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        Xh = X.cpu().pin_memory()
+        Yh = torch.zeros_like(Xh).pin_memory()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            B.ccsd_jacobian_transform(h, 0, args.nvec, Xh, Yh)
+            B.ccsd_jacobian_transform(h, 1, args.nvec, Xh, Yh)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([el], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        nbytes = 2 * args.nvec * dim * 8
+        e2e = {"value": n_tr / el, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    peaks, src = load_peaks()
+    peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    ladder_alg = ladder_flops_per_vector(o, v) * args.nvec
+    top_ms = prof["top_ms"] / max(prof["top_launches"], 1)
+    achieved = ladder_alg / (top_ms * 1e-3) / 1e12 if top_ms > 0 else 0.0
+    issued = prof["top_issued_flops"] / max(prof["top_launches"], 1) / (top_ms * 1e-3) / 1e12 if top_ms > 0 else 0.0
+    executed = prof["top_flops"] / max(prof["top_launches"], 1) / (top_ms * 1e-3) / 1e12 if top_ms > 0 else 0.0
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_tc_gemm<256> (pp-ladder contraction)",
+                "peak_source": f"bf16_tflops_sustained of {src} MEASURED_PEAKS.json",
+                "algorithmic_flops_per_launch": ladder_alg,
+                "executed_tflops": executed, "issued_tflops": issued, "issued_frac": issued / peak,
+                "launch_ms": top_ms,
+                "all_tc": {"launches": prof["tc_launches"], "ms": prof["tc_ms"], "alg_tflops":
+                           prof["tc_flops"] / max(prof["tc_ms"], 1e-9) / 1e9,
+                           "issued_tflops": prof["tc_issued_flops"] / max(prof["tc_ms"], 1e-9) / 1e9},
+                "fp64_gemm": {"launches": prof["fp64_launches"], "ms": prof["fp64_ms"],
+                              "tflops": prof["fp64_flops"] / max(prof["fp64_ms"], 1e-9) / 1e9}}
+    f_alg, _ = transform_flops(o, v, naux)
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None,
+           "dtype": "f64 (bf16x%d split tensor-core products, fp32 accumulate)" % (3 if args.splits == 2 else 6)
+           if prec == B.PREC_MIXED else "f64",
+           "data": "synthetic",
+           "config": {"workload": f"{args.workload} o={o} v={v} naux={naux}", "nvec": args.nvec,
+                      "step": f"right + left block transform of {args.nvec} vectors",
+                      "precision": args.precision, "splits": args.splits,
+                      "l2": "inputs larger than L2 (vvvv integrals 21.6 GB)"},
+           "right_transforms_per_s": right_rate, "left_transforms_per_s": left_rate,
+           "alg_tflops_per_transform": f_alg / 1e12,
+           "alg_tflops": value * f_alg / 1e12 / world,
+           "setup": {"ground_iters": iters, "e_ccsd": e_ccsd, "ground_seconds": t_setup},
+           "roofline": roofline, "e2e": e2e, "gpu_launches": prof["launches"], "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_entry(o, v, naux)
+    B.ccsd_destroy(h)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -73,6 +73,7 @@ typedef struct {
   int davidson_max_sub; /* subspace size before restart */
   int guess;            /* CCSD_GUESS_MP2 */
   void* stream;         /* cudaStream_t, 0 = default */
+  double tc_min_flops;  /* mixed mode: contractions below this many flops stay FP64 */
 } ccsd_options;
 
 /* Fill *opt with defaults (FP64, tol_res 1e-10, tol_eom 1e-7, tol_lin 1e-9, ...). */
@@ -138,6 +139,24 @@ ccsd_status ccsd_derivative_coupling(ccsd_handle h, int k, int l, int ndir, cons
 /* Seconds spent in the last call and counters of the executor (GEMM calls,
  * tensor-core calls and their flops) since creation; any pointer may be NULL. */
 ccsd_status ccsd_stats(ccsd_handle h, double* flops_fp64, double* flops_tc, long long* gemms, long long* tc_gemms);
+
+/* Kernel-level profile of the calls made between ccsd_profile_start and
+ * ccsd_profile_stop: every GEMM launch is bracketed by CUDA events on the
+ * handle's stream (small overhead, no extra synchronisation until stop).
+ * flops are algorithmic (2 M N K per contraction); tc_issued_flops are the
+ * tensor-core MMA flops actually issued (split products and padding).  The
+ * "top" fields cover the largest tensor-core contraction (the pp-ladder). */
+typedef struct {
+  long long launches;         /* kernels launched by the library */
+  long long tc_launches;      /* tcgen05 GEMM launches */
+  double tc_ms, tc_flops, tc_issued_flops;
+  long long fp64_launches;    /* FP64 GEMM launches */
+  double fp64_ms, fp64_flops;
+  long long top_launches;
+  double top_ms, top_flops, top_issued_flops;
+} ccsd_profile_data;
+ccsd_status ccsd_profile_start(ccsd_handle h);
+ccsd_status ccsd_profile_stop(ccsd_handle h, ccsd_profile_data* out);
 
 const char* ccsd_strerror(ccsd_status s);
 const char* ccsd_last_error(ccsd_handle h);

@@ -35,6 +35,24 @@ class Options(ctypes.Structure):
         ("davidson_max_sub", ctypes.c_int),
         ("guess", ctypes.c_int),
         ("stream", ctypes.c_void_p),
+        ("tc_min_flops", ctypes.c_double),
+    ]
+
+
+class ProfileData(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_longlong),
+        ("tc_launches", ctypes.c_longlong),
+        ("tc_ms", ctypes.c_double),
+        ("tc_flops", ctypes.c_double),
+        ("tc_issued_flops", ctypes.c_double),
+        ("fp64_launches", ctypes.c_longlong),
+        ("fp64_ms", ctypes.c_double),
+        ("fp64_flops", ctypes.c_double),
+        ("top_launches", ctypes.c_longlong),
+        ("top_ms", ctypes.c_double),
+        ("top_flops", ctypes.c_double),
+        ("top_issued_flops", ctypes.c_double),
     ]
 
 
@@ -70,6 +88,10 @@ def lib():
         L.ccsd_coupling_densities.argtypes = [_P, ctypes.c_int, ctypes.c_int, _P, _P]
         L.ccsd_derivative_coupling.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _D]
         L.ccsd_stats.argtypes = [_P, _D, _D, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]
+        L.ccsd_profile_start.argtypes = [_P]
+        L.ccsd_profile_start.restype = ctypes.c_int
+        L.ccsd_profile_stop.argtypes = [_P, ctypes.POINTER(ProfileData)]
+        L.ccsd_profile_stop.restype = ctypes.c_int
         L.ccsd_strerror.argtypes = [ctypes.c_int]
         L.ccsd_strerror.restype = ctypes.c_char_p
         L.ccsd_last_error.argtypes = [_P]
@@ -187,6 +209,16 @@ def ccsd_stats(h):
     g, gt = ctypes.c_longlong(), ctypes.c_longlong()
     _check(h, lib().ccsd_stats(h, ctypes.byref(f64), ctypes.byref(ftc), ctypes.byref(g), ctypes.byref(gt)))
     return {"flops_fp64": f64.value, "flops_tc": ftc.value, "gemms": g.value, "tc_gemms": gt.value}
+
+
+def ccsd_profile_start(h):
+    _check(h, lib().ccsd_profile_start(h))
+
+
+def ccsd_profile_stop(h) -> dict:
+    d = ProfileData()
+    _check(h, lib().ccsd_profile_stop(h, ctypes.byref(d)))
+    return {name: getattr(d, name) for name, _ in ProfileData._fields_}
 
 
 def ccsd_destroy(h):

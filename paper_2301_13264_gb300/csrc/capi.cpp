@@ -86,6 +86,7 @@ struct ccsd_ctx {
   // densities of the last pair
   int dens_k = -1, dens_l = -1;
   DevBuf Dd, Zd;
+  long long prof_launch0 = 0;
 };
 
 namespace {
@@ -439,6 +440,8 @@ ccsd_status guarded(ccsd_ctx* c, F&& f) {
     return CCSD_OK;
   } catch (const Err& e) {
     return fail(c, e.code, e.what());
+  } catch (const DeviceTimeout& e) {
+    return fail(c, CCSD_ERR_TIMEOUT, e.what());
   } catch (const std::bad_alloc& e) {
     return fail(c, CCSD_ERR_OOM, "host allocation failed");
   } catch (const std::exception& e) {
@@ -543,6 +546,7 @@ void ccsd_default_options(ccsd_options* opt) {
   opt->davidson_max_sub = 48;
   opt->guess = CCSD_GUESS_MP2;
   opt->stream = nullptr;
+  opt->tc_min_flops = 2.0e9;
 }
 
 const char* ccsd_strerror(ccsd_status s) {
@@ -626,6 +630,7 @@ ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int
     c->ex.reset(new Executor(cp.g, o, v, naux, 16, c->st));
     Executor& ex = *c->ex;
     ex.set_precision(c->opt.precision, c->opt.splits);
+    ex.tc_min_flops = c->opt.tc_min_flops;
     ex.bind(cp.h, c->h.p);
     ex.bind(cp.B, c->B.p);
     ex.bind(cp.ones_o, c->ones.p);
@@ -635,6 +640,8 @@ ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int
       if (t == cp.O1 || t == cp.O2 || t == cp.E) continue;
       ex.alloc_persistent(t);
     }
+    ex.const_tensors = {cp.h, cp.B, cp.ones_o};
+    for (const Op& op : cp.fwd_const) ex.const_tensors.insert(op.out.t);
     ex.run(cp.fwd_const);
     sync(c);
   });
@@ -878,6 +885,35 @@ ccsd_status ccsd_stats(ccsd_handle c, double* flops_fp64, double* flops_tc, long
     if (flops_tc) *flops_tc = c->ex->stats.tc_flops;
     if (gemms) *gemms = c->ex->stats.gemm_calls;
     if (tc_gemms) *tc_gemms = c->ex->stats.tc_calls;
+  });
+}
+
+ccsd_status ccsd_profile_start(ccsd_handle c) {
+  return guarded(c, [&] {
+    c->ex->collect();
+    c->ex->profile(true);
+    c->prof_launch0 = kernel_launches();
+  });
+}
+
+ccsd_status ccsd_profile_stop(ccsd_handle c, ccsd_profile_data* out) {
+  return guarded(c, [&] {
+    Executor::ProfTotals t = c->ex->collect();
+    c->ex->profile(false);
+    if (out) {
+      out->launches = kernel_launches() - c->prof_launch0;
+      out->tc_launches = t.tc_launches;
+      out->tc_ms = t.tc_ms;
+      out->tc_flops = t.tc_flops;
+      out->tc_issued_flops = t.tc_issued;
+      out->fp64_launches = t.fp64_launches;
+      out->fp64_ms = t.fp64_ms;
+      out->fp64_flops = t.fp64_flops;
+      out->top_launches = t.top_launches;
+      out->top_ms = t.top_ms;
+      out->top_flops = t.top_flops;
+      out->top_issued_flops = t.top_issued;
+    }
   });
 }
 

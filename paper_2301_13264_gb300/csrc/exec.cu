@@ -303,23 +303,24 @@ void Executor::exec_contract(const Op& op) {
   if (Bt > 65535 || M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) throw std::runtime_error("GEMM too large");
   double flops = 2.0 * (double)Bt * M * N * K;
   bool done = false;
+  ProfRec rec{};
+  if (profiling_) {
+    CK(cudaEventCreate(&rec.a));
+    CK(cudaEventCreate(&rec.b));
+    CK(cudaEventRecord(rec.a, st_));
+    rec.flops = flops;
+  }
   if (prec_ == PREC_MIXED && flops >= tc_min_flops) {
-    bool b_const = (g_.T[op.b.t].role == ROLE_INPUT_H) && (Bpack == nullptr);
-    (void)b_const;
+    bool a_const = const_tensors.count(op.a.t) && Apack == nullptr;
+    bool b_const = const_tensors.count(op.b.t) && Bpack == nullptr;
     done = tc_contract((int)Bt, (int)M, (int)N, (int)K, Ap, sAb, sAm, sAk, Bp, sBb, sBn, sBk, Cp, sCb, sCm, sCn,
-                       alpha, false);
-    if (!cdirect && !done) {
-      // tc path writes C = alpha*AB + C; Ctmp must be zero for beta = 0 semantics
-    }
+                       alpha, beta, a_const, b_const);
     if (done) {
       stats.tc_calls++;
       stats.tc_flops += flops;
     }
   }
   if (!done) {
-    if (!cdirect) {
-      // plain GEMM overwrites Ctmp (beta = 0)
-    }
     GemmArgs ga;
     ga.batch = (int)Bt;
     ga.M = (int)M;
@@ -343,6 +344,12 @@ void Executor::exec_contract(const Op& op) {
     stats.gemm_calls++;
     stats.gemm_flops += flops;
   }
+  if (profiling_) {
+    CK(cudaEventRecord(rec.b, st_));
+    rec.tc = done;
+    rec.issued = done ? last_tc_issued : flops;
+    prof_.push_back(rec);
+  }
   if (!cdirect) {
     Strided sp;
     std::vector<char> order = bat;
@@ -362,6 +369,42 @@ void Executor::exec_contract(const Op& op) {
   if (Apack) tmp_free(Apack);
   if (Bpack) tmp_free(Bpack);
   if (Ctmp) tmp_free(Ctmp);
+}
+
+void Executor::profile(bool on) {
+  if (!on) collect();
+  profiling_ = on;
+}
+
+Executor::ProfTotals Executor::collect() {
+  ProfTotals t;
+  CK(cudaStreamSynchronize(st_));
+  double top = 0.0;
+  for (const ProfRec& r : prof_) if (r.tc) top = std::max(top, r.flops);
+  for (const ProfRec& r : prof_) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    if (r.tc) {
+      t.tc_launches++;
+      t.tc_ms += ms;
+      t.tc_flops += r.flops;
+      t.tc_issued += r.issued;
+      if (r.flops == top) {
+        t.top_launches++;
+        t.top_ms += ms;
+        t.top_flops += r.flops;
+        t.top_issued += r.issued;
+      }
+    } else {
+      t.fp64_launches++;
+      t.fp64_ms += ms;
+      t.fp64_flops += r.flops;
+    }
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  prof_.clear();
+  return t;
 }
 
 void Executor::exec_axpy(const Op& op) {
@@ -401,6 +444,7 @@ void Executor::run(const Prog& p) {
     last_use[op.a.t] = i;
     if (op.kind == 'C') last_use[op.b.t] = i;
   }
+  const int64_t tc_calls_at_start = stats.tc_calls;
   std::set<int> run_temps;
   for (auto& kv : first_write) {
     int t = kv.first;
@@ -466,6 +510,10 @@ void Executor::run(const Prog& p) {
     cudaEventDestroy(ev1);
   }
   CK(cudaGetLastError());
+  if (stats.tc_calls != tc_calls_at_start) {
+    int f = tc_error();
+    if (f != 0) throw DeviceTimeout("a tensor-core kernel wait exceeded its budget");
+  }
 }
 
 }  // namespace ccsd

@@ -12,6 +12,7 @@
 
 #include <cstdint>
 #include <set>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -95,13 +96,44 @@ class Executor {
   int64_t scratch_n_ = 0;
   size_t cache_bytes_ = 0;
 
+  int* tc_err_ = nullptr;  // device flag raised by a tensor-core kernel whose wait timed out
+  struct ProfRec {
+    cudaEvent_t a, b;
+    double flops, issued;
+    bool tc;
+  };
+  bool profiling_ = false;
+  std::vector<ProfRec> prof_;
+
  public:
-  // tensor-core path (tc_gemm.cu); returns false when the op is not eligible
+  // tensor-core path (tc_gemm.cu); returns false when the op is not eligible.
+  // C = alpha * A B^T + beta * C with beta in {0, 1}; constant operands keep
+  // their bf16 slices cached for the life of the executor.
   bool tc_contract(int batch, int M, int N, int K, const double* A, int64_t sAb, int64_t sAm, int64_t sAk,
                    const double* B, int64_t sBb, int64_t sBn, int64_t sBk, double* C, int64_t sCb, int64_t sCm,
-                   int64_t sCn, double alpha, bool b_const);
+                   int64_t sCn, double alpha, double beta, bool a_const, bool b_const);
+  // value of the device error flag (synchronises the stream); 0 when no tensor-core kernel ran
+  int tc_error();
+  // tensors whose values never change after set-up (their bf16 slices may be cached)
+  std::set<int> const_tensors;
+  // Profiling: when on, every GEMM launch is bracketed by CUDA events on the
+  // executor's stream; collect() returns per-engine totals and clears the records.
+  struct ProfTotals {
+    long long tc_launches = 0, fp64_launches = 0;
+    double tc_ms = 0, tc_flops = 0, tc_issued = 0, fp64_ms = 0, fp64_flops = 0;
+    double top_ms = 0, top_flops = 0, top_issued = 0;  // the largest tensor-core contraction
+    long long top_launches = 0;
+  };
+  void profile(bool on);
+  ProfTotals collect();
+  double last_tc_issued = 0.0;  // MMA flops of the last tensor-core launch (padding included)
   struct CacheEntry;
   std::vector<CacheEntry*> cache_;
+};
+
+// A device-side wait exceeded its budget (the kernel raised its error flag).
+struct DeviceTimeout : std::runtime_error {
+  explicit DeviceTimeout(const std::string& m) : std::runtime_error(m) {}
 };
 
 }  // namespace ccsd

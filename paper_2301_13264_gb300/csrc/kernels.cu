@@ -3,9 +3,14 @@
 #include "kernels.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <stdexcept>
 
 namespace ccsd {
+
+static std::atomic<long long> g_launches{0};
+long long kernel_launches() { return g_launches.load(); }
+void count_launches(int n) { g_launches.fetch_add(n); }
 
 static inline int grid_for(int64_t n, int block = 256, int cap = 152 * 16) {
   int64_t g = (n + block - 1) / block;
@@ -55,6 +60,7 @@ __global__ void k_zero_strided(double* __restrict__ dst, Strided sp, I total) {
 void launch_axpy_strided(double* dst, const double* src, const Strided& sp, double alpha, cudaStream_t st) {
   int64_t n = sp.total();
   if (n == 0) return;
+  count_launches(1);
   if (n < (int64_t(1) << 31))
     k_axpy_strided<uint32_t, false><<<grid_for(n), 256, 0, st>>>(dst, src, sp, (uint32_t)n, alpha);
   else
@@ -64,6 +70,7 @@ void launch_axpy_strided(double* dst, const double* src, const Strided& sp, doub
 void launch_copy_strided(double* dst, const double* src, const Strided& sp, cudaStream_t st) {
   int64_t n = sp.total();
   if (n == 0) return;
+  count_launches(1);
   if (n < (int64_t(1) << 31))
     k_axpy_strided<uint32_t, true><<<grid_for(n), 256, 0, st>>>(dst, src, sp, (uint32_t)n, 1.0);
   else
@@ -73,6 +80,7 @@ void launch_copy_strided(double* dst, const double* src, const Strided& sp, cuda
 void launch_zero_strided(double* dst, const Strided& sp, cudaStream_t st) {
   int64_t n = sp.total();
   if (n == 0) return;
+  count_launches(1);
   if (n < (int64_t(1) << 31))
     k_zero_strided<uint32_t><<<grid_for(n), 256, 0, st>>>(dst, sp, (uint32_t)n);
   else
@@ -214,10 +222,89 @@ __global__ void k_split_reduce(GemmArgs g, int nsplit, const double* __restrict_
   }
 }
 
+static void launch_dgemm_chunk(const GemmArgs& g, cudaStream_t st);
+
 void launch_dgemm(const GemmArgs& g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return;
   if (g.K <= 0) throw std::runtime_error("dgemm: K must be positive");
   if (g.batch > 65535) throw std::runtime_error("dgemm: batch too large");
+  // the M tiles index grid.y (<= 65535): split very tall products into row chunks
+  const int64_t max_rows = (int64_t)65535 * DT;
+  if (g.M > max_rows) {
+    for (int64_t m0 = 0; m0 < g.M; m0 += max_rows) {
+      GemmArgs c = g;
+      c.M = (int)std::min<int64_t>(max_rows, g.M - m0);
+      c.A = g.A + m0 * g.sAm;
+      c.C = g.C + m0 * g.sCm;
+      launch_dgemm_chunk(c, st);
+    }
+    return;
+  }
+  launch_dgemm_chunk(g, st);
+}
+
+// Matrix-vector shapes (N == 1): one warp per output row, lanes stride over K.
+__global__ void __launch_bounds__(256) k_dgemv(GemmArgs g) {
+  const int warps = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t rows = (int64_t)g.batch * g.M;
+  for (int64_t r = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * warps) {
+    const int64_t b = r / g.M, m = r % g.M;
+    const double* A = g.A + b * g.sAb + m * g.sAm;
+    const double* B = g.B + b * g.sBb;
+    double s = 0.0;
+    for (int64_t k = lane; k < g.K; k += 32) s = fma(A[k * g.sAk], B[k * g.sBk], s);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+      double* c = g.C + b * g.sCb + m * g.sCm;
+      *c = g.alpha * s + (g.beta != 0.0 ? g.beta * (*c) : 0.0);
+    }
+  }
+}
+
+// Rank-1 shapes (K == 1): C[b][m][n] = alpha A[b][m] B[b][n] + beta C.
+__global__ void k_drank1(GemmArgs g) {
+  const int64_t tot = (int64_t)g.batch * g.M * g.N;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = idx / ((int64_t)g.M * g.N);
+    const int64_t r = idx % ((int64_t)g.M * g.N);
+    const int64_t m = r / g.N, n = r % g.N;
+    const double v = g.alpha * g.A[b * g.sAb + m * g.sAm] * g.B[b * g.sBb + n * g.sBn];
+    double* c = g.C + b * g.sCb + m * g.sCm + n * g.sCn;
+    *c = v + (g.beta != 0.0 ? g.beta * (*c) : 0.0);
+  }
+}
+
+static void launch_dgemm_chunk(const GemmArgs& g, cudaStream_t st) {
+  if (g.K == 1) {
+  count_launches(1);
+    k_drank1<<<grid_for((int64_t)g.batch * g.M * g.N), 256, 0, st>>>(g);
+    return;
+  }
+  if (g.N == 1 && (int64_t)g.M * g.batch >= 64) {
+  count_launches(1);
+    k_dgemv<<<grid_for((int64_t)g.batch * g.M * 32), 256, 0, st>>>(g);
+    return;
+  }
+  if (g.M == 1 && (int64_t)g.N * g.batch >= 64) {
+  count_launches(1);
+    GemmArgs t = g;  // C^T = B A^T: swap the roles of A and B
+    t.M = g.N;
+    t.N = 1;
+    t.A = g.B;
+    t.sAb = g.sBb;
+    t.sAm = g.sBn;
+    t.sAk = g.sBk;
+    t.B = g.A;
+    t.sBb = g.sAb;
+    t.sBn = g.sAm;
+    t.sBk = g.sAk;
+    t.sCm = g.sCn;
+    t.sCn = g.sCm;
+    k_dgemv<<<grid_for((int64_t)t.batch * t.M * 32), 256, 0, st>>>(t);
+    return;
+  }
   const int target = 2 * 152;
   const int64_t outputs = (int64_t)g.M * g.N;
   if (outputs <= 64 && g.batch <= 64 && g.K >= 4096) {
@@ -228,6 +315,7 @@ void launch_dgemm(const GemmArgs& g, cudaStream_t st) {
     size_t bytes = (size_t)nsplit * g.batch * outputs * sizeof(double);
     if (cudaMallocAsync((void**)&part, bytes, st) != cudaSuccess) throw std::runtime_error("dgemm: workspace");
     dim3 grid((unsigned)nsplit, (unsigned)outputs, g.batch);
+    count_launches(2);
     k_ddot_split<<<grid, 256, 0, st>>>(g, (int)nsplit, kchunk, part);
     k_split_reduce<<<grid_for(g.batch * outputs), 256, 0, st>>>(g, (int)nsplit, part);
     cudaFreeAsync(part, st);
@@ -243,6 +331,7 @@ void launch_dgemm(const GemmArgs& g, cudaStream_t st) {
     while ((int64_t)g.batch * nsplit > 65535) --nsplit;
   }
   if (nsplit == 1) {
+  count_launches(1);
     dim3 grid((unsigned)tn, (unsigned)tm, g.batch);
     k_dgemm<<<grid, 256, 0, st>>>(g, 1, g.K, nullptr);
     return;
@@ -254,6 +343,7 @@ void launch_dgemm(const GemmArgs& g, cudaStream_t st) {
   size_t bytes = (size_t)nsplit * g.batch * g.M * g.N * sizeof(double);
   if (cudaMallocAsync((void**)&part, bytes, st) != cudaSuccess) throw std::runtime_error("dgemm: workspace");
   dim3 grid((unsigned)tn, (unsigned)tm, (unsigned)(g.batch * nsplit));
+  count_launches(2);
   k_dgemm<<<grid, 256, 0, st>>>(g, nsplit, kchunk, part);
   k_split_reduce<<<grid_for((int64_t)g.batch * g.M * g.N), 256, 0, st>>>(g, nsplit, part);
   cudaFreeAsync(part, st);
@@ -339,6 +429,7 @@ void launch_wdot(const VecShape& s, const double* X, int64_t ldx, int np, const 
   if (np <= 0 || nq <= 0) return;
   int nch = wdot_chunks();
   dim3 grid(nch, (np + TP - 1) / TP, (nq + TQ - 1) / TQ);
+  count_launches(2);
   k_wdot_partial<<<grid, WD_BLOCK, 0, st>>>(s, X, ldx, np, Y, ldy, nq, work);
   k_wdot_final<<<(np * nq + 127) / 128, 128, 0, st>>>(nch, np, nq, work, G, ldg);
 }
@@ -368,6 +459,7 @@ __global__ void k_lincomb(int64_t dim, const double* __restrict__ X, int64_t ldx
 
 void launch_lincomb(const VecShape& s, const double* X, int64_t ldx, int np, const double* c, int ldc, double* Y,
                     int64_t ldy, int nq, bool accumulate, cudaStream_t st) {
+  count_launches(1);
   int64_t dim = s.dim();
   k_lincomb<<<grid_for(dim), 256, 0, st>>>(dim, X, ldx, np, c, ldc, Y, ldy, nq, accumulate);
 }
@@ -378,7 +470,10 @@ __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, doubl
 }
 
 void launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st) {
-  if (n > 0) k_axpby<<<grid_for(n), 256, 0, st>>>(n, a, x, b, y);
+  if (n > 0) {
+    count_launches(1);
+    k_axpby<<<grid_for(n), 256, 0, st>>>(n, a, x, b, y);
+  }
 }
 
 __global__ void k_precond(VecShape s, const double* __restrict__ eps, const double* __restrict__ x,
@@ -406,6 +501,7 @@ __global__ void k_precond(VecShape s, const double* __restrict__ eps, const doub
 void launch_precond(const VecShape& s, const double* eps, const double* x, double* y, double shift,
                     cudaStream_t st) {
   k_precond<<<grid_for(s.dim()), 256, 0, st>>>(s, eps, x, y, shift);
+  count_launches(1);
 }
 
 __global__ void k_weight(VecShape s, const double* __restrict__ x, double* __restrict__ y, int nvec, int64_t ld) {
@@ -418,6 +514,7 @@ __global__ void k_weight(VecShape s, const double* __restrict__ x, double* __res
 }
 
 void launch_weight(const VecShape& s, const double* x, double* y, int nvec, int64_t ld, cudaStream_t st) {
+  count_launches(1);
   k_weight<<<grid_for(s.dim() * nvec), 256, 0, st>>>(s, x, y, nvec, ld);
 }
 
@@ -452,6 +549,7 @@ __global__ void k_packed_grad(VecShape s, const double* __restrict__ g, double* 
 
 void launch_packed_grad(const VecShape& s, const double* g, double* y, int nvec, int64_t ld, cudaStream_t st) {
   if (g == y) throw std::runtime_error("packed_grad must be out of place");
+  count_launches(1);
   k_packed_grad<<<grid_for(s.dim() * nvec), 256, 0, st>>>(s, g, y, nvec, ld);
 }
 
@@ -507,12 +605,14 @@ __global__ void k_maxabs_final(int nb, const double* work, const double* x, doub
 
 void launch_maxabs(int64_t n, const double* x, double* out, double* work, cudaStream_t st) {
   int nb = 256;
+  count_launches(2);
   k_maxabs_partial<<<nb, 256, 0, st>>>(n, x, work, 0);
   k_maxabs_final<<<1, 32, 0, st>>>(nb, work, x, out, 0);
 }
 
 void launch_argmaxabs(int64_t n, const double* x, double* out, double* work, cudaStream_t st) {
   int nb = 256;
+  count_launches(2);
   k_maxabs_partial<<<nb, 256, 0, st>>>(n, x, work, 1);
   k_maxabs_final<<<1, 32, 0, st>>>(nb, work, x, out, 1);
 }
@@ -540,6 +640,7 @@ __global__ void k_sum_final(int nb, const double* work, double* out) {
 
 void launch_dot(int64_t n, const double* x, const double* y, double* out, double* work, cudaStream_t st) {
   int nb = 512;
+  count_launches(2);
   k_dot_partial<<<nb, 256, 0, st>>>(n, x, y, work);
   k_sum_final<<<1, 32, 0, st>>>(nb, work, out);
 }
@@ -572,6 +673,7 @@ __global__ void k_tau_singles(VecShape s, double r0, const double* __restrict__ 
 
 void launch_tau_expectation(const VecShape& s, double r0, const double* L, const double* R, double* y,
                             cudaStream_t st) {
+  count_launches(2);
   k_tau_singles<<<s.o * s.v, 256, 0, st>>>(s, r0, L, R, y);
   int64_t n2 = s.dim() - s.n1();
   k_axpby<<<grid_for(n2), 256, 0, st>>>(n2, r0, L + s.n1(), 0.0, y + s.n1());

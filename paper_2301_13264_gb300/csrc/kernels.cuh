@@ -9,6 +9,10 @@ namespace ccsd {
 
 constexpr int kMaxDims = 8;
 
+// Number of kernels this library has launched (all streams, all handles).
+long long kernel_launches();
+void count_launches(int n);
+
 // A strided index space: ndim dims with extents, plus per-dim strides of up to
 // two addressed arrays.  Linear index -> row-major coordinates over ext.
 struct Strided {

@@ -1,10 +1,330 @@
 // Tensor-core (tcgen05) contraction path for the mixed-precision mode.
+//
+// An FP64 contraction C += alpha * A B^T (A: M x K, B: N x K) is evaluated as a
+// sum of bf16 products: each FP64 operand is split into S bf16 slices
+// x = x_0 + x_1 (+ x_2) (x_0 = bf16(x), x_1 = bf16(x - x_0), ...), and the
+// products x_i y_j with i + j < S are accumulated in one FP32 TMEM accumulator
+// (S = 2: 3 products, ~16 significant bits; S = 3: 6 products, ~24 bits).
+// The slices live in a [S][rows][Kp] bf16 array (K padded to the 64-element
+// tile with zeros); a 3-D TMA map selects the slice with its third coordinate,
+// so the products are simply more K iterations of the same mainloop.
+//
+// Kernel: one 128 x BN output tile per CTA (BN = 64, 128 or 256), 4 warps.  Warp 0
+// lane 0 issues TMA loads into a 4- or 6-stage ring (mbarrier full/empty pairs),
+// warp 1 lane 0 issues tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulate,
+// 128 x BN x 16 per instruction) and commits each stage back to the producer; after the last
+// commit all four warps read the accumulator with tcgen05.ld (warp w owns TMEM
+// lanes 32w..32w+31) and add alpha * acc into the FP64 output.  Every mbarrier
+// wait is bounded; on timeout the kernel raises a device error flag, drains its
+// own copies and MMAs (bounded), frees TMEM and exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <utility>
+
 #include "exec.h"
 
 namespace ccsd {
 
+namespace tc {
+
+constexpr int BM = 128, BK = 64, NTHREADS = 128;
+constexpr int A_BYTES = BM * BK * 2;
+// per tile width BN (64, 128 or 256): B tile bytes, pipeline depth, shared memory
+template <int BN>
+struct Cfg {
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int STAGES = (BN == 256) ? 4 : 6;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+};
+constexpr long long TIMEOUT_CYCLES = 4000000000LL;  // about 2 s at 2 GHz
+constexpr int MAXPROD = 6;
+
+struct Params {
+  int M, N;
+  int kt_per_prod;  // 64-wide K tiles per slice
+  int nprod;
+  int pa[MAXPROD], pb[MAXPROD];
+  double* C;
+  long long sCm, sCn;
+  double alpha;
+  int beta_zero;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity; false on timeout or when
+// another CTA has raised the error flag.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* err) {
+  long long t0 = clock64();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255u) == 255u) {
+      if (*err) return false;
+      if (clock64() - t0 > TIMEOUT_CYCLES) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
+                                            int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  // K-major operand tile, rows of 64 bf16 (128 B), 128-byte swizzle:
+  // start address >> 4, leading-byte offset 16 B (unused with this swizzle),
+  // stride-byte offset 1024 B between 8-row groups, descriptor version 1,
+  // layout type 2 = SWIZZLE_128B.
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, bf16 A and B, both K-major,
+// N = BN (bits 17-22 hold N/8), M = 128 (bits 24-28 hold M/16).
+template <int BN>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idsc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idsc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, Params p) {
+  constexpr int STAGES = Cfg<BN>::STAGES, B_BYTES = Cfg<BN>::B_BYTES, STAGE_BYTES = Cfg<BN>::STAGE_BYTES;
+  extern __shared__ uint8_t smem_raw[];
+  volatile int* err = p.err;
+  if (*err) return;
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int iters = p.nprod * p.kt_per_prod;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ta)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tb)) : "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int issued = 0;
+      bool ok = true;
+      for (int it = 0; it < iters; ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, err)) {
+          ok = false;
+          break;
+        }
+        const int prod = it / p.kt_per_prod, kt = it % p.kt_per_prod;
+        mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+        tma_load_3d(smem_u32(sA + s * A_BYTES), &ta, full0 + 8 * s, kt * BK, m0, p.pa[prod]);
+        tma_load_3d(smem_u32(sB + s * B_BYTES), &tb, full0 + 8 * s, kt * BK, n0, p.pb[prod]);
+        ++issued;
+      }
+      if (!ok) {
+        atomicExch((int*)p.err, 1);
+        // drain this CTA's copies still in flight (bounded)
+        for (int it = issued - 1; it >= 0 && it >= issued - STAGES; --it) {
+          const int s = it % STAGES;
+          const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+          long long t0 = clock64();
+          while (!mbar_try_wait(full0 + 8 * s, ph) && clock64() - t0 < TIMEOUT_CYCLES) {
+          }
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = true;
+      for (int it = 0; it < iters; ++it) {
+        const int s = it % STAGES;
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        if (!mbar_wait(full0 + 8 * s, ph, err)) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+#pragma unroll
+        for (int j = 0; j < BK / 16; ++j)
+          mma_bf16(tmem, smem_desc(a0 + 32 * j), smem_desc(b0 + 32 * j), idesc<BN>(), (it | j) != 0 ? 1u : 0u);
+        mma_commit(empty0 + 8 * s);
+      }
+      if (!ok) atomicExch((int*)p.err, 1);
+      mma_commit(done);  // fires once every issued MMA has completed
+    }
+    __syncwarp();
+  }
+
+  // epilogue: TMEM -> registers -> FP64 output
+  const bool ready = mbar_wait(done, 0, err);
+  fence_after();
+  if (!ready) atomicExch((int*)p.err, 1);
+  if (ready && !*err) {
+    const int row = m0 + warp * 32 + lane;
+    double* crow = p.C + (long long)row * p.sCm;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+      if (row < p.M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c + j;
+          if (n < p.N) {
+            double* dst = crow + (long long)n * p.sCn;
+            const double v = p.alpha * (double)__uint_as_float(r[j]);
+            *dst = p.beta_zero ? v : (*dst + v);
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+  }
+}
+
+// FP64 -> S bf16 slices, dst[s][row][Kp] (K tail zero-filled by the caller).
+__global__ void k_split_pack(const double* __restrict__ src, int64_t rows, int64_t K, int64_t srow, int64_t sk, int S,
+                             int64_t Kp, int64_t plane, __nv_bfloat16* __restrict__ dst) {
+  const int64_t total = rows * K;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = idx / K, k = idx % K;
+    double x = src[r * srow + k * sk];
+    __nv_bfloat16* d = dst + r * Kp + k;
+    for (int s = 0; s < S; ++s) {
+      __nv_bfloat16 b = __double2bfloat16(x);
+      d[s * plane] = b;
+      x -= (double)__bfloat162float(b);
+    }
+  }
+}
+
+typedef CUresult (*EncodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      throw std::runtime_error("cuTensorMapEncodeTiled unavailable");
+    fn = (EncodeTiled)p;
+  }
+  return fn;
+}
+
+static CUtensorMap make_map(const void* base, int64_t rows, int64_t Kp, int S, int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)S};
+  cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encoder()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw std::runtime_error("cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return m;
+}
+
+}  // namespace tc
+
 struct Executor::CacheEntry {
   const double* src = nullptr;
+  int64_t rows = 0, rows_p = 0, K = 0, srow = 0, sk = 0;
+  int S = 0;
   void* dev = nullptr;
   size_t bytes = 0;
 };
@@ -16,11 +336,128 @@ void Executor::clear_cache() {
   }
   cache_.clear();
   cache_bytes_ = 0;
+  if (tc_err_) {
+    cudaFree(tc_err_);
+    tc_err_ = nullptr;
+  }
 }
 
-bool Executor::tc_contract(int, int, int, int, const double*, int64_t, int64_t, int64_t, const double*, int64_t,
-                           int64_t, int64_t, double*, int64_t, int64_t, int64_t, double, bool) {
-  return false;
+int Executor::tc_error() {
+  if (!tc_err_) return 0;
+  int h = 0;
+  if (cudaMemcpyAsync(&h, tc_err_, sizeof(int), cudaMemcpyDeviceToHost, st_) != cudaSuccess) return -1;
+  if (cudaStreamSynchronize(st_) != cudaSuccess) return -1;
+  return h;
+}
+
+// bf16 slices [S][rows][Kp] of an FP64 operand (cached when the operand is constant)
+// The slice planes have rows_p >= rows rows (a multiple of the TMA box) and
+// Kp >= K columns; the padding is zero so it adds nothing to the products.
+static __nv_bfloat16* make_slices(cudaStream_t st, const double* src, int64_t rows, int64_t rows_p, int64_t K,
+                                  int64_t srow, int64_t sk, int S, int64_t Kp) {
+  size_t bytes = (size_t)S * rows_p * Kp * sizeof(__nv_bfloat16);
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) throw std::runtime_error("tc operand allocation failed");
+  if (Kp != K || rows_p != rows) cudaMemsetAsync(p, 0, bytes, st);
+  int64_t total = rows * K;
+  int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+  count_launches(1);
+  tc::k_split_pack<<<grid, 256, 0, st>>>(src, rows, K, srow, sk, S, Kp, rows_p * Kp, (__nv_bfloat16*)p);
+  return (__nv_bfloat16*)p;
+}
+
+template <int BN>
+static void launch_tc(dim3 grid, const CUtensorMap& ta, const CUtensorMap& tb, const tc::Params& p, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(tc::k_tc_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::Cfg<BN>::SMEM_BYTES);
+    attr = true;
+  }
+  count_launches(1);
+  tc::k_tc_gemm<BN><<<grid, tc::NTHREADS, tc::Cfg<BN>::SMEM_BYTES, st>>>(ta, tb, p);
+}
+
+bool Executor::tc_contract(int batch, int M, int N, int K, const double* A, int64_t sAb, int64_t sAm, int64_t sAk,
+                           const double* B, int64_t sBb, int64_t sBn, int64_t sBk, double* C, int64_t sCb,
+                           int64_t sCm, int64_t sCn, double alpha, double beta, bool a_const, bool b_const) {
+  (void)sAb;
+  (void)sBb;
+  (void)sCb;
+  if (batch != 1 || M < 1 || N < 1 || K < 1) return false;
+  if (beta != 0.0 && beta != 1.0) return false;
+  // the MMA tile is 128 rows of A by BN rows of B: put the longer side on A
+  if (M < tc::BM && N > M) {
+    std::swap(M, N);
+    std::swap(A, B);
+    std::swap(sAm, sBn);
+    std::swap(sAk, sBk);
+    std::swap(a_const, b_const);
+    std::swap(sCm, sCn);
+  }
+  const int BN = (N > 128) ? 256 : (N > 64 ? 128 : 64);
+  const int S = (splits_ >= 3) ? 3 : 2;
+  const int64_t Kp = ((int64_t)K + tc::BK - 1) / tc::BK * tc::BK;
+  const int64_t Mp = ((int64_t)M + tc::BM - 1) / tc::BM * tc::BM;
+  const int64_t Np = ((int64_t)N + BN - 1) / BN * BN;
+  if (Np / BN > 65535) return false;
+  if (!tc_err_) {
+    if (cudaMalloc(&tc_err_, sizeof(int)) != cudaSuccess) throw std::runtime_error("tc flag allocation failed");
+    cudaMemsetAsync(tc_err_, 0, sizeof(int), st_);
+  }
+  auto get = [&](const double* src, int64_t rows, int64_t rows_p, int64_t srow, int64_t sk, bool cst, bool& owned) {
+    if (cst) {
+      for (CacheEntry* e : cache_)
+        if (e->src == src && e->rows == rows && e->rows_p == rows_p && e->K == K && e->srow == srow &&
+            e->sk == sk && e->S == S) {
+          owned = false;
+          return (__nv_bfloat16*)e->dev;
+        }
+    }
+    __nv_bfloat16* p = make_slices(st_, src, rows, rows_p, K, srow, sk, S, Kp);
+    owned = !cst;
+    if (cst) {
+      CacheEntry* e = new CacheEntry{src, rows, rows_p, (int64_t)K, srow, sk, S, p, (size_t)S * rows_p * Kp * 2};
+      cache_.push_back(e);
+      cache_bytes_ += e->bytes;
+    }
+    return p;
+  };
+  bool ownA = false, ownB = false;
+  __nv_bfloat16* a = get(A, M, Mp, sAm, sAk, a_const, ownA);
+  __nv_bfloat16* b = get(B, N, Np, sBn, sBk, b_const, ownB);
+  CUtensorMap ta = tc::make_map(a, Mp, Kp, S, tc::BM);
+  CUtensorMap tb = tc::make_map(b, Np, Kp, S, BN);
+  tc::Params p;
+  p.M = M;
+  p.N = N;
+  p.kt_per_prod = (int)(Kp / tc::BK);
+  // products x_i y_j with i + j < S
+  const int pa3[3] = {0, 0, 1}, pb3[3] = {0, 1, 0};
+  const int pa6[6] = {0, 0, 1, 0, 1, 2}, pb6[6] = {0, 1, 0, 2, 1, 0};
+  p.nprod = (S == 2) ? 3 : 6;
+  for (int i = 0; i < p.nprod; ++i) {
+    p.pa[i] = (S == 2) ? pa3[i] : pa6[i];
+    p.pb[i] = (S == 2) ? pb3[i] : pb6[i];
+  }
+  p.C = C;
+  p.sCm = sCm;
+  p.sCn = sCn;
+  p.alpha = alpha;
+  p.beta_zero = (beta == 0.0) ? 1 : 0;
+  p.err = tc_err_;
+  dim3 grid((unsigned)(Mp / tc::BM), (unsigned)(Np / BN));
+  last_tc_issued = 2.0 * (double)Mp * (double)Np * (double)Kp * p.nprod;
+  if (BN == 256)
+    launch_tc<256>(grid, ta, tb, p, st_);
+  else if (BN == 128)
+    launch_tc<128>(grid, ta, tb, p, st_);
+  else
+    launch_tc<64>(grid, ta, tb, p, st_);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw std::runtime_error(std::string("tc gemm launch: ") + cudaGetErrorString(e));
+  if (ownA) cudaFreeAsync(a, st_);
+  if (ownB) cudaFreeAsync(b, st_);
+  return true;
 }
 
 }  // namespace ccsd

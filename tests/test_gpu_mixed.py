@@ -1,0 +1,152 @@
+"""Mixed-precision (tcgen05 split-bf16) path against the FP64 oracle.
+
+The tensor-core products carry ~16 significant bits with two bf16 slices per
+operand (3 products) and ~24 bits with three slices (6 products), accumulated
+in FP32.  Residuals and transforms are compared element-wise with the oracle
+at a tolerance derived from that: the error of a contraction is bounded by
+2^-b times the sum of |a||b| terms, which for these inputs stays within 4e-4
+(two slices) and 4e-6 (three slices) of the largest element.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ccsd as cc
+from oracle.solvers import System, Vec
+from paper_2301_13264_gb300 import binding as B
+from paper_2301_13264_gb300.synth import make_hamiltonian, random_amplitudes, workload
+
+pytestmark = pytest.mark.gpu
+
+TOL = {2: 4e-4, 3: 4e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    assert torch.cuda.is_available()
+    B.lib()
+
+
+def flat(x1, x2):
+    return np.concatenate([np.asarray(x1).reshape(-1), np.asarray(x2).reshape(-1)])
+
+
+def relerr(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max()
+
+
+def mixed(H, S, **kw):
+    opt = B.ccsd_default_options(precision=B.PREC_MIXED, splits=S, tc_min_flops=0.0, **kw)
+    return B.ccsd_create(H.eps, H.h, H.B, H.o, H.v, H.naux, opt)
+
+
+@pytest.mark.parametrize("S", [2, 3])
+@pytest.mark.parametrize("o,v,naux", [(6, 48, 60), (9, 37, 41)])
+def test_mixed_residual_and_transforms(S, o, v, naux):
+    H = make_hamiltonian(o, v, naux, seed=4)
+    X1, X2 = random_amplitudes(o, v, 8, scale=0.03, nvec=4)
+    t = flat(X1[0], X2[0])
+    h = mixed(H, S)
+    try:
+        om = np.zeros_like(t)
+        e = B.ccsd_residual(h, t, om)
+        st = B.ccsd_stats(h)
+        assert st["tc_gemms"] > 0, "tensor-core path not taken"
+        c1, c2, ce = cc.residual(cc.as_t(X1[0]), cc.as_t(X2[0]), cc.as_t(H.h), cc.as_t(H.B), o)
+        assert relerr(om, flat(c1, c2)) < TOL[S]
+        # with tc_min_flops = 0 the Fock-matrix contractions run on the tensor cores too
+        assert abs(e - float(ce)) < TOL[S] * abs(float(ce))
+        B.ccsd_set_amplitudes(h, t, np.zeros_like(t))
+        X = np.stack([flat(X1[k], X2[k]) for k in (1, 2, 3)])
+        YR, YL = np.zeros_like(X), np.zeros_like(X)
+        B.ccsd_jacobian_transform(h, 0, 3, X, YR)
+        B.ccsd_jacobian_transform(h, 1, 3, X, YL)
+    finally:
+        B.ccsd_destroy(h)
+    S_ = System(H.eps, H.h, H.B, o)
+    tv = Vec(cc.as_t(X1[0]), cc.as_t(X2[0]))
+    for k in range(3):
+        r = Vec(cc.as_t(X1[k + 1]), cc.as_t(X2[k + 1]))
+        ar, la = S_.right(tv, r), S_.left(tv, r)
+        assert relerr(YR[k], flat(ar.x1, ar.x2)) < TOL[S]
+        assert relerr(YL[k], flat(la.x1, la.x2)) < TOL[S]
+
+
+def test_mixed_pipeline_energy_and_couplings():
+    """Three-slice products with FP64 solver arithmetic: energies within 1e-7 Eh
+    and couplings within 1e-4 relative of the oracle at the small workload."""
+    H = workload("small")
+    S_ = System(H.eps, H.h, H.B, H.o)
+    res = S_.run(2, tol=1e-12, tol_eom=1e-10, tol_lin=1e-12)
+    h = mixed(H, 3, tol_res=1e-10, tol_eom=1e-8, tol_lin=1e-10, max_iter=200)
+    try:
+        e, _ = B.ccsd_solve_ground(h)
+        w, _ = B.eom_solve_right(h, 2)
+        B.eom_solve_left(h, 2)
+        F = {kl: B.ccsd_derivative_coupling(h, kl[0], kl[1], 1, H.h1, H.B1)[0] for kl in [(1, 2), (0, 1), (2, 0)]}
+        assert B.ccsd_stats(h)["tc_gemms"] > 0
+    finally:
+        B.ccsd_destroy(h)
+    assert abs(e - res.e_ccsd) < 1e-7
+    assert np.abs(np.array(w) - np.array(res.omega)).max() < 1e-6
+    for (k, l), f in F.items():
+        ref = S_.coupling(res, k, l, H.h1, H.B1, tol_lin=1e-12)
+        assert abs(f - ref) < 1e-4 * abs(ref)
+
+
+@pytest.mark.parametrize("S", [3])
+def test_thymine_adz_residual_full_size(S):
+    """o=33, v=228, naux=900 (the throughput workload): element-wise parity of
+    the mixed residual with the oracle at random amplitudes."""
+    H = workload("thymine_adz")
+    o, v = H.o, H.v
+    x1, x2 = random_amplitudes(o, v, 21, scale=0.01)
+    t = flat(x1[0], x2[0])
+    h = mixed(H, S, tc_min_flops=2.0e9)
+    try:
+        om = np.zeros_like(t)
+        e = B.ccsd_residual(h, t, om)
+    finally:
+        B.ccsd_destroy(h)
+    c1, c2, ce = cc.residual(cc.as_t(x1[0]), cc.as_t(x2[0]), cc.as_t(H.h), cc.as_t(H.B), o, vvvv_batch=24)
+    assert relerr(om, flat(c1, c2)) < TOL[S]
+    assert abs(e - float(ce)) < 1e-8
+
+
+def test_thymine_adz_transform_properties():
+    """At full size: <L|A R> = <L^T A|R> and A R matches the central difference
+    of the residual along R (properties that hold at any size)."""
+    H = workload("thymine_adz")
+    o, v = H.o, H.v
+    X1, X2 = random_amplitudes(o, v, 22, scale=0.01, nvec=3)
+    t = torch.as_tensor(flat(X1[0], X2[0]), device="cuda")
+    R = torch.as_tensor(flat(X1[1], X2[1]), device="cuda")[None]
+    L = torch.as_tensor(flat(X1[2], X2[2]), device="cuda")[None]
+    h = mixed(H, 3, tc_min_flops=2.0e9)
+    try:
+        B.ccsd_set_amplitudes(h, t, torch.zeros_like(t))
+        AR, LA = torch.zeros_like(R), torch.zeros_like(L)
+        B.ccsd_jacobian_transform(h, 0, 1, R, AR)
+        B.ccsd_jacobian_transform(h, 1, 1, L, LA)
+        w = torch.as_tensor(cc.pair_weight(o, v).numpy().reshape(-1), device="cuda")
+
+        def pdot(a, b):
+            n1 = o * v
+            return float((a[:n1] * b[:n1]).sum() + (w * a[n1:] * b[n1:]).sum())
+
+        lhs, rhs = pdot(L[0], AR[0]), pdot(LA[0], R[0])
+        assert abs(lhs - rhs) < 1e-5 * max(abs(lhs), 1e-12)
+    finally:
+        B.ccsd_destroy(h)
+    # central difference of the FP64 residual (the mixed residual's rounding is
+    # not smooth in t, so the difference quotient uses the FP64 path)
+    h64 = B.ccsd_create(H.eps, H.h, H.B, o, v, H.naux, B.ccsd_default_options())
+    try:
+        d = 1e-3
+        op, om_ = torch.zeros_like(t), torch.zeros_like(t)
+        B.ccsd_residual(h64, t + d * R[0], op)
+        B.ccsd_residual(h64, t - d * R[0], om_)
+        fd = (op - om_) / (2 * d)
+        assert float((fd - AR[0]).abs().max() / AR[0].abs().max()) < 1e-4
+    finally:
+        B.ccsd_destroy(h64)
