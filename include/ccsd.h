@@ -136,6 +136,26 @@ ccsd_status ccsd_coupling_densities(ccsd_handle h, int k, int l, double* D, doub
 ccsd_status ccsd_derivative_coupling(ccsd_handle h, int k, int l, int ndir, const double* dh, const double* dB,
                                      double* F);
 
+/* Allocation-free variant of ccsd_derivative_coupling (the paper has no
+ * counterpart; this is a service for callers that cannot allocate device
+ * memory at this point, e.g. a dynamics loop running inside a memory pool owned
+ * by another framework, or one that must not touch the allocator between time
+ * steps because an allocation can synchronise the device).
+ * F[d] = sum_pq D_pq dh[d]_pq + sum_Jpq Z_Jpq dB[d]_Jpq with the densities the
+ * handle already holds: call ccsd_coupling_densities(h, k, l, ...) first,
+ * otherwise CCSD_ERR_STATE.  dh[ndir][n*n] and dB[ndir][naux*n*n] must be device
+ * memory (CCSD_ERR_ARG otherwise); F[ndir] may be host or device memory.
+ * 1 <= ndir <= 256 (CCSD_ERR_ARG otherwise).
+ * Allocates nothing: the reduction scratch is a fixed 16 KiB array in the
+ * library's device image (one per GPU that loads the library, kept until the
+ * process exits).  Its device address is looked up on the first call made on
+ * each device, with that device current: make that first call before any CUDA
+ * stream capture.  All calls share the array, so calls whose GPU work overlaps
+ * (different streams or threads) race and may return wrong values; serialise
+ * them.  Synchronises the handle's stream. */
+ccsd_status ccsd_derivative_coupling_noalloc(ccsd_handle h, int k, int l, int ndir, const double* dh,
+                                             const double* dB, double* F);
+
 /* Seconds spent in the last call and counters of the executor (GEMM calls,
  * tensor-core calls and their flops) since creation; any pointer may be NULL. */
 ccsd_status ccsd_stats(ccsd_handle h, double* flops_fp64, double* flops_tc, long long* gemms, long long* tc_gemms);

@@ -204,6 +204,17 @@ def ccsd_derivative_coupling(h, k, l, ndir, dh, dB):
     return list(F)
 
 
+def ccsd_derivative_coupling_noalloc(h, k, l, ndir, dh, dB):
+    """Allocation-free variant; dh and dB must be device tensors, densities held."""
+    F = (ctypes.c_double * ndir)()
+    L = lib()
+    if not getattr(L.ccsd_derivative_coupling_noalloc, "argtypes", None):
+        L.ccsd_derivative_coupling_noalloc.argtypes = [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _D]
+        L.ccsd_derivative_coupling_noalloc.restype = ctypes.c_int
+    _check(h, L.ccsd_derivative_coupling_noalloc(h, k, l, ndir, _ptr(dh), _ptr(dB), F))
+    return list(F)
+
+
 def ccsd_stats(h):
     f64, ftc = ctypes.c_double(), ctypes.c_double()
     g, gt = ctypes.c_longlong(), ctypes.c_longlong()

@@ -888,6 +888,28 @@ ccsd_status ccsd_stats(ccsd_handle c, double* flops_fp64, double* flops_tc, long
   });
 }
 
+}  // extern "C"
+
+namespace ccsd {
+// Internal accessor for noalloc.cu: the densities of the pair (k, l) if they are
+// the ones held by the handle, with the sizes and stream.  Allocates nothing.
+bool held_densities(ccsd_handle c, int k, int l, const double** D, const double** Z, int* n, int* naux,
+                    cudaStream_t* st) {
+  if (!c || c->dens_k != k || c->dens_l != l || !c->Dd.p || !c->Zd.p) return false;
+  *D = c->Dd.p;
+  *Z = c->Zd.p;
+  *n = c->n;
+  *naux = c->naux;
+  *st = c->st;
+  return true;
+}
+void set_error(ccsd_handle c, const char* msg) {
+  if (c) c->err = msg;
+}
+}  // namespace ccsd
+
+extern "C" {
+
 ccsd_status ccsd_profile_start(ccsd_handle c) {
   return guarded(c, [&] {
     c->ex->collect();
