@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--nvec", type=int, default=8)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--splits", type=int, default=3)
+    ap.add_argument("--amplitudes", choices=["solve", "synthetic"], default="solve",
+                    help="converge the ground state in set-up, or use seeded synthetic amplitudes")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -208,7 +210,12 @@ def run_ours(args, rank, world, local_rank):
                                  max_iter=100)
     h = B.ccsd_create(H.eps, H.h, H.B, o, v, naux, opt)
     t_setup = time.perf_counter()
-    e_ccsd, iters = B.ccsd_solve_ground(h)
+    if args.amplitudes == "solve":
+        e_ccsd, iters = B.ccsd_solve_ground(h)
+    else:
+        T1, T2 = random_amplitudes(o, v, 999, scale=0.01)
+        tt = torch.as_tensor(np.concatenate([T1.reshape(-1), T2.reshape(-1)]), device="cuda")
+        e_ccsd, iters = B.ccsd_set_amplitudes(h, tt, torch.zeros_like(tt)), 0
     t_setup = time.perf_counter() - t_setup
     X1, X2 = random_amplitudes(o, v, 1000 + rank, scale=0.01, nvec=args.nvec)
     X = torch.as_tensor(np.concatenate([X1.reshape(args.nvec, -1), X2.reshape(args.nvec, -1)], axis=1),
@@ -280,17 +287,21 @@ def run_ours(args, rank, world, local_rank):
 
     peaks, src = load_peaks()
     peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    # pp-ladder: two tensor-core GEMMs (the + and - parts) per ladder contraction,
+    # one contraction per block transform side
     ladder_alg = ladder_flops_per_vector(o, v) * args.nvec
-    top_ms = prof["top_ms"] / max(prof["top_launches"], 1)
-    achieved = ladder_alg / (top_ms * 1e-3) / 1e12 if top_ms > 0 else 0.0
-    issued = prof["top_issued_flops"] / max(prof["top_launches"], 1) / (top_ms * 1e-3) / 1e12 if top_ms > 0 else 0.0
-    executed = prof["top_flops"] / max(prof["top_launches"], 1) / (top_ms * 1e-3) / 1e12 if top_ms > 0 else 0.0
+    n_ladder = max(prof["ladder_launches"] // 2, 1)
+    lad_ms = prof["ladder_ms"] / n_ladder
+    achieved = ladder_alg / (lad_ms * 1e-3) / 1e12 if lad_ms > 0 else 0.0
+    issued = prof["ladder_issued_flops"] / n_ladder / (lad_ms * 1e-3) / 1e12 if lad_ms > 0 else 0.0
+    executed = prof["ladder_flops"] / n_ladder / (lad_ms * 1e-3) / 1e12 if lad_ms > 0 else 0.0
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_tc_gemm<256> (pp-ladder contraction)",
+                "traffic": None, "kernel": "k_tc_gemm<256> (pp-ladder, +/- GEMM pair)",
                 "peak_source": f"bf16_tflops_sustained of {src} MEASURED_PEAKS.json",
                 "algorithmic_flops_per_launch": ladder_alg,
+                "algorithmic_definition": "o^2 v^4 / 4 multiply-adds per vector (pair-packed ladder) x nvec",
                 "executed_tflops": executed, "issued_tflops": issued, "issued_frac": issued / peak,
-                "launch_ms": top_ms,
+                "launch_ms": lad_ms, "ladder_launches": prof["ladder_launches"],
                 "all_tc": {"launches": prof["tc_launches"], "ms": prof["tc_ms"], "alg_tflops":
                            prof["tc_flops"] / max(prof["tc_ms"], 1e-9) / 1e9,
                            "issued_tflops": prof["tc_issued_flops"] / max(prof["tc_ms"], 1e-9) / 1e9},

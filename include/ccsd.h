@@ -174,6 +174,8 @@ typedef struct {
   double fp64_ms, fp64_flops;
   long long top_launches;
   double top_ms, top_flops, top_issued_flops;
+  long long ladder_launches;  /* particle-particle ladder GEMMs (two per ladder contraction) */
+  double ladder_ms, ladder_flops, ladder_issued_flops;
 } ccsd_profile_data;
 ccsd_status ccsd_profile_start(ccsd_handle h);
 ccsd_status ccsd_profile_stop(ccsd_handle h, ccsd_profile_data* out);

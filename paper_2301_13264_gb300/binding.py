@@ -53,6 +53,10 @@ class ProfileData(ctypes.Structure):
         ("top_ms", ctypes.c_double),
         ("top_flops", ctypes.c_double),
         ("top_issued_flops", ctypes.c_double),
+        ("ladder_launches", ctypes.c_longlong),
+        ("ladder_ms", ctypes.c_double),
+        ("ladder_flops", ctypes.c_double),
+        ("ladder_issued_flops", ctypes.c_double),
     ]
 
 

@@ -216,26 +216,23 @@ void hess_right(ccsd_ctx* c, double g0, const double* g, const double* r, double
 struct Diis {
   ccsd_ctx* c;
   int cap;
-  std::vector<std::unique_ptr<DevBuf>> X, E;
+  DevBuf X, E;             // [cap][dim] ring buffers of vectors and errors
   std::vector<double> Bm;  // cap x cap Gram matrix of stored errors
   int m = 0, next = 0;
   Diis(ccsd_ctx* c_, int cap_) : c(c_), cap(std::max(cap_, 1)), Bm(cap * cap, 0.0) {
-    for (int i = 0; i < cap; ++i) {
-      X.emplace_back(new DevBuf(c->dim));
-      E.emplace_back(new DevBuf(c->dim));
-    }
+    X.alloc(cap * c->dim);
+    E.alloc(cap * c->dim);
   }
   // store (x, e) and write the extrapolated vector to out
   void step(const double* x, const double* e, double* out) {
     int slot = next;
     next = (next + 1) % cap;
     m = std::min(m + 1, cap);
-    CUDA_OK(cudaMemcpyAsync(X[slot]->p, x, c->dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-    CUDA_OK(cudaMemcpyAsync(E[slot]->p, e, c->dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-    for (int q = 0; q < m; ++q) {
-      std::vector<double> d = gram(c, E[q]->p, c->dim, 1, E[slot]->p, c->dim, 1);
-      Bm[q * cap + slot] = Bm[slot * cap + q] = d[0];
-    }
+    const int64_t dim = c->dim;
+    CUDA_OK(cudaMemcpyAsync(X.p + slot * dim, x, dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    CUDA_OK(cudaMemcpyAsync(E.p + slot * dim, e, dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    std::vector<double> d = gram(c, E.p, dim, m, E.p + slot * dim, dim, 1);
+    for (int q = 0; q < m; ++q) Bm[q * cap + slot] = Bm[slot * cap + q] = d[q];
     if (m < 2) {
       CUDA_OK(cudaMemcpyAsync(out, x, c->dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
       return;
@@ -255,11 +252,8 @@ struct Diis {
       return;
     }
     // slots 0..m-1 hold the stored vectors (ring buffer, all valid once m == cap)
-    std::vector<double> coef(m);
-    for (int i = 0; i < m; ++i) coef[i] = b[i];
-    // gather pointers: X slots are separate buffers; combine one at a time
-    launch_axpby(c->dim, coef[0], X[0]->p, 0.0, out, c->st);
-    for (int i = 1; i < m; ++i) launch_axpby(c->dim, coef[i], X[i]->p, 1.0, out, c->st);
+    std::vector<double> coef(b.begin(), b.begin() + m);
+    lincomb(c, X.p, dim, m, coef, out, dim, 1, false);
   }
 };
 
@@ -640,6 +634,7 @@ ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int
       if (t == cp.O1 || t == cp.O2 || t == cp.E) continue;
       ex.alloc_persistent(t);
     }
+    ex.ladder_w_ = cp.g.id("W");
     ex.const_tensors = {cp.h, cp.B, cp.ones_o};
     for (const Op& op : cp.fwd_const) ex.const_tensors.insert(op.out.t);
     ex.run(cp.fwd_const);
@@ -935,6 +930,10 @@ ccsd_status ccsd_profile_stop(ccsd_handle c, ccsd_profile_data* out) {
       out->top_ms = t.top_ms;
       out->top_flops = t.top_flops;
       out->top_issued_flops = t.top_issued;
+      out->ladder_launches = t.ladder_launches;
+      out->ladder_ms = t.ladder_ms;
+      out->ladder_flops = t.ladder_flops;
+      out->ladder_issued_flops = t.ladder_issued;
     }
   });
 }

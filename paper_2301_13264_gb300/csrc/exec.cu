@@ -188,6 +188,7 @@ static bool collapse(const std::vector<char>& group, const std::map<char, std::p
 }
 
 void Executor::exec_contract(const Op& op) {
+  if (try_ladder(op)) return;
   SView O = resolve(op.out), A = resolve(op.a), B = resolve(op.b);
   auto lo = merge(O, op.lo), la = merge(A, op.la), lb = merge(B, op.lb);
   std::map<char, std::pair<int64_t, int64_t>> eo, ea, eb;
@@ -236,6 +237,94 @@ void Executor::exec_contract(const Op& op) {
   for (char c : Kl) K *= ext_of(c);
   if (Bt == 0 || M == 0 || N == 0) return;
   if (K == 0) return;
+  if (Bt > 65535 || M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) throw std::runtime_error("GEMM too large");
+  const double flops = 2.0 * (double)Bt * M * N * K;
+
+  // output addressing: direct when the out view has the [bat][M][N] shape
+  int64_t sCb, sCm, sCn;
+  const bool cdirect = collapse(bat, eo, sCb) && collapse(Ml, eo, sCm) && collapse(Nl, eo, sCn);
+  auto scatter_from = [&](const double* Ctmp) {
+    Strided sp;
+    std::vector<char> order = bat;
+    order.insert(order.end(), Ml.begin(), Ml.end());
+    order.insert(order.end(), Nl.begin(), Nl.end());
+    sp.ndim = (int)order.size();
+    int64_t st = 1;
+    for (int d = sp.ndim - 1; d >= 0; --d) {
+      sp.ext[d] = eo[order[d]].first;
+      sp.s0[d] = eo[order[d]].second;
+      sp.s1[d] = st;
+      st *= sp.ext[d];
+    }
+    launch_axpy_strided(O.base, Ctmp, sp, op.alpha, st_);
+    stats.scatters++;
+  };
+
+  // tensor-core path: operands are gathered straight from their strided FP64
+  // layout into bf16 slices (no FP64 staging copy)
+  if (prec_ == PREC_MIXED && flops >= tc_min_flops && Bt == 1) {
+    auto gather = [&](std::map<char, std::pair<int64_t, int64_t>>& es, const std::vector<char>& rows) {
+      Strided g;
+      std::vector<char> order = rows;
+      order.insert(order.end(), Kl.begin(), Kl.end());
+      g.ndim = (int)order.size();
+      for (int d = 0; d < g.ndim; ++d) {
+        g.ext[d] = es[order[d]].first;
+        g.s1[d] = es[order[d]].second;
+        g.s0[d] = 0;
+      }
+      return g;
+    };
+    Strided ag = gather(ea, Ml), bg = gather(eb, Nl);
+    const bool a_const = const_tensors.count(op.a.t) > 0, b_const = const_tensors.count(op.b.t) > 0;
+    // non-contiguous outputs are addressed by the GEMM epilogue through the output's own strides
+    Strided om, on;
+    auto out_dims = [&](const std::vector<char>& labels, Strided& g) {
+      g.ndim = (int)labels.size();
+      for (int d = 0; d < g.ndim; ++d) {
+        g.ext[d] = eo[labels[d]].first;
+        g.s0[d] = eo[labels[d]].second;
+        g.s1[d] = 0;
+      }
+      if (g.ndim == 0) {
+        g.ndim = 1;
+        g.ext[0] = 1;
+        g.s0[0] = g.s1[0] = 0;
+      }
+    };
+    if (!cdirect) {
+      out_dims(Ml, om);
+      out_dims(Nl, on);
+    }
+    double* Ct = nullptr;
+    ProfRec rec{};
+    if (profiling_) {
+      CK(cudaEventCreate(&rec.a));
+      CK(cudaEventCreate(&rec.b));
+      CK(cudaEventRecord(rec.a, st_));
+      rec.flops = flops;
+    }
+    bool ok = tc_contract((int)M, (int)N, (int)K, A.base, ag, B.base, bg, O.base, cdirect ? sCm : 0,
+                          cdirect ? sCn : 0, op.alpha, 1.0, a_const, b_const, cdirect ? nullptr : &om,
+                          cdirect ? nullptr : &on);
+    if (profiling_) {
+      CK(cudaEventRecord(rec.b, st_));
+      rec.tc = ok;
+      rec.issued = ok ? last_tc_issued : 0.0;
+      if (ok)
+        prof_.push_back(rec);
+      else {
+        cudaEventDestroy(rec.a);
+        cudaEventDestroy(rec.b);
+      }
+    }
+    if (ok) {
+      stats.tc_calls++;
+      stats.tc_flops += flops;
+      return;
+    }
+    if (Ct) tmp_free(Ct);
+  }
 
   // operand A: [bat][M][K]
   const double* Ap = A.base;
@@ -286,8 +375,6 @@ void Executor::exec_contract(const Op& op) {
     sBn = K;
     sBk = 1;
   }
-  int64_t sCb, sCm, sCn;
-  bool cdirect = collapse(bat, eo, sCb) && collapse(Ml, eo, sCm) && collapse(Nl, eo, sCn);
   double* Ctmp = nullptr;
   double* Cp = O.base;
   double alpha = op.alpha, beta = 1.0;
@@ -300,9 +387,6 @@ void Executor::exec_contract(const Op& op) {
     alpha = 1.0;
     beta = 0.0;
   }
-  if (Bt > 65535 || M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) throw std::runtime_error("GEMM too large");
-  double flops = 2.0 * (double)Bt * M * N * K;
-  bool done = false;
   ProfRec rec{};
   if (profiling_) {
     CK(cudaEventCreate(&rec.a));
@@ -310,62 +394,35 @@ void Executor::exec_contract(const Op& op) {
     CK(cudaEventRecord(rec.a, st_));
     rec.flops = flops;
   }
-  if (prec_ == PREC_MIXED && flops >= tc_min_flops) {
-    bool a_const = const_tensors.count(op.a.t) && Apack == nullptr;
-    bool b_const = const_tensors.count(op.b.t) && Bpack == nullptr;
-    done = tc_contract((int)Bt, (int)M, (int)N, (int)K, Ap, sAb, sAm, sAk, Bp, sBb, sBn, sBk, Cp, sCb, sCm, sCn,
-                       alpha, beta, a_const, b_const);
-    if (done) {
-      stats.tc_calls++;
-      stats.tc_flops += flops;
-    }
-  }
-  if (!done) {
-    GemmArgs ga;
-    ga.batch = (int)Bt;
-    ga.M = (int)M;
-    ga.N = (int)N;
-    ga.K = (int)K;
-    ga.A = Ap;
-    ga.sAb = sAb;
-    ga.sAm = sAm;
-    ga.sAk = sAk;
-    ga.B = Bp;
-    ga.sBb = sBb;
-    ga.sBn = sBn;
-    ga.sBk = sBk;
-    ga.C = Cp;
-    ga.sCb = sCb;
-    ga.sCm = sCm;
-    ga.sCn = sCn;
-    ga.alpha = alpha;
-    ga.beta = beta;
-    launch_dgemm(ga, st_);
-    stats.gemm_calls++;
-    stats.gemm_flops += flops;
-  }
+  GemmArgs ga;
+  ga.batch = (int)Bt;
+  ga.M = (int)M;
+  ga.N = (int)N;
+  ga.K = (int)K;
+  ga.A = Ap;
+  ga.sAb = sAb;
+  ga.sAm = sAm;
+  ga.sAk = sAk;
+  ga.B = Bp;
+  ga.sBb = sBb;
+  ga.sBn = sBn;
+  ga.sBk = sBk;
+  ga.C = Cp;
+  ga.sCb = sCb;
+  ga.sCm = sCm;
+  ga.sCn = sCn;
+  ga.alpha = alpha;
+  ga.beta = beta;
+  launch_dgemm(ga, st_);
+  stats.gemm_calls++;
+  stats.gemm_flops += flops;
   if (profiling_) {
     CK(cudaEventRecord(rec.b, st_));
-    rec.tc = done;
-    rec.issued = done ? last_tc_issued : flops;
+    rec.tc = false;
+    rec.issued = flops;
     prof_.push_back(rec);
   }
-  if (!cdirect) {
-    Strided sp;
-    std::vector<char> order = bat;
-    order.insert(order.end(), Ml.begin(), Ml.end());
-    order.insert(order.end(), Nl.begin(), Nl.end());
-    sp.ndim = (int)order.size();
-    int64_t st = 1;
-    for (int d = sp.ndim - 1; d >= 0; --d) {
-      sp.ext[d] = eo[order[d]].first;
-      sp.s0[d] = eo[order[d]].second;
-      sp.s1[d] = st;
-      st *= sp.ext[d];
-    }
-    launch_axpy_strided(O.base, Ctmp, sp, op.alpha, st_);
-    stats.scatters++;
-  }
+  if (!cdirect) scatter_from(Ctmp);
   if (Apack) tmp_free(Apack);
   if (Bpack) tmp_free(Bpack);
   if (Ctmp) tmp_free(Ctmp);
@@ -384,6 +441,12 @@ Executor::ProfTotals Executor::collect() {
   for (const ProfRec& r : prof_) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    if (r.ladder) {
+      t.ladder_launches++;
+      t.ladder_ms += ms;
+      t.ladder_flops += r.flops;
+      t.ladder_issued += r.issued;
+    }
     if (r.tc) {
       t.tc_launches++;
       t.tc_ms += ms;

@@ -24,7 +24,7 @@ namespace ccsd {
 enum Precision : int { PREC_FP64 = 0, PREC_MIXED = 1 };
 
 struct ExecStats {
-  int64_t gemm_calls = 0, tc_calls = 0, packs = 0, scatters = 0, axpys = 0;
+  int64_t gemm_calls = 0, tc_calls = 0, packs = 0, scatters = 0, axpys = 0, ladders = 0;
   double gemm_flops = 0.0, tc_flops = 0.0;
 };
 
@@ -101,17 +101,40 @@ class Executor {
     cudaEvent_t a, b;
     double flops, issued;
     bool tc;
+    bool ladder = false;
   };
   bool profiling_ = false;
   std::vector<ProfRec> prof_;
 
  public:
   // tensor-core path (tc_gemm.cu); returns false when the op is not eligible.
-  // C = alpha * A B^T + beta * C with beta in {0, 1}; constant operands keep
-  // their bf16 slices cached for the life of the executor.
-  bool tc_contract(int batch, int M, int N, int K, const double* A, int64_t sAb, int64_t sAm, int64_t sAk,
-                   const double* B, int64_t sBb, int64_t sBn, int64_t sBk, double* C, int64_t sCb, int64_t sCm,
-                   int64_t sCn, double alpha, double beta, bool a_const, bool b_const);
+  // C = alpha * A B^T + beta * C with beta in {0, 1}.  A and B are strided
+  // gathers over (row dims..., K dims...) with source strides in s1; constant
+  // operands keep their bf16 slices cached for the life of the executor.
+  // With om/on given, element (m, n) is written at C + off(m; om) + off(n; on) (row-major
+  // decomposition over ext, strides in s0) instead of C + m*sCm + n*sCn.
+  bool tc_contract(int M, int N, int K, const double* A, const Strided& Ag, const double* B, const Strided& Bg,
+                   double* C, int64_t sCm, int64_t sCn, double alpha, double beta, bool a_const, bool b_const,
+                   const Strided* om = nullptr, const Strided* on = nullptr);
+  // tcgen05 GEMM on prepared bf16 slices: a [S][Mp][Kp], b [S][Np][Kp] (rows and K
+  // zero-padded; Mp a multiple of 128, Np of the tile width chosen for N);
+  // C[m*sCm + n*sCn] = alpha * sum + beta * C.
+  void tc_run(const void* a, int64_t Mp, const void* b, int64_t Np, int K, int64_t Kp, int S, int M, int N, double* C,
+              int64_t sCm, int64_t sCn, double alpha, double beta, const Strided* om = nullptr,
+              const Strided* on = nullptr);
+  // pp-ladder contractions against the bare vvvv tensor (ladder.cu); false if op is not one
+  bool try_ladder(const Op& op);
+  int ladder_w_ = -1;  // tensor id of W[a][b][c][d] = (ac|bd)
+  const int2* pair_table();
+  struct WPM {
+    bool mixed = false;
+    int S = 0;
+    void *plus = nullptr, *minus = nullptr;
+    int64_t rows_p = 0, ld = 0;
+    size_t bytes = 0;
+  };
+  std::vector<WPM> wpm_;
+  void* pairs_ = nullptr;
   // value of the device error flag (synchronises the stream); 0 when no tensor-core kernel ran
   int tc_error();
   // tensors whose values never change after set-up (their bf16 slices may be cached)
@@ -123,6 +146,8 @@ class Executor {
     double tc_ms = 0, tc_flops = 0, tc_issued = 0, fp64_ms = 0, fp64_flops = 0;
     double top_ms = 0, top_flops = 0, top_issued = 0;  // the largest tensor-core contraction
     long long top_launches = 0;
+    double ladder_ms = 0, ladder_flops = 0, ladder_issued = 0;  // pp-ladder GEMMs
+    long long ladder_launches = 0;
   };
   void profile(bool on);
   ProfTotals collect();

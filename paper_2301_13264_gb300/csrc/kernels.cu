@@ -367,8 +367,13 @@ __device__ __forceinline__ double pair_weight(const VecShape& s, int64_t k) {
   return (i == j && a == b) ? 1.0 : 0.5;
 }
 
-constexpr int TP = 8, TQ = 8, WD_BLOCK = 256;
+// Packed inner products.  The pair weight is 1 on singles, 1/2 on doubles and 1 on
+// the doubles diagonal (ai = bj), so <x|y> = sum_singles x y + 1/2 sum_doubles x y
+// + 1/2 sum_diagonal x y: the partial kernel weighs by position only (no index
+// arithmetic per element) and the final kernel adds the o*v diagonal terms.
+constexpr int WD_BLOCK = 256;
 
+template <int TP, int TQ>
 __global__ void __launch_bounds__(WD_BLOCK) k_wdot_partial(VecShape s, const double* __restrict__ X, int64_t ldx,
                                                            int np, const double* __restrict__ Y, int64_t ldy, int nq,
                                                            double* __restrict__ work) {
@@ -379,45 +384,72 @@ __global__ void __launch_bounds__(WD_BLOCK) k_wdot_partial(VecShape s, const dou
   for (int p = 0; p < TP; ++p)
 #pragma unroll
     for (int q = 0; q < TQ; ++q) acc[p][q] = 0.0;
-  const int64_t dim = s.dim();
+  const int64_t dim = s.dim(), n1 = s.n1();
+  const double* Xp[TP];
+  const double* Yq[TQ];
+#pragma unroll
+  for (int p = 0; p < TP; ++p) Xp[p] = X + (int64_t)(p0 + min(p, pn - 1)) * ldx;
+#pragma unroll
+  for (int q = 0; q < TQ; ++q) Yq[q] = Y + (int64_t)(q0 + min(q, qn - 1)) * ldy;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < dim; k += (int64_t)gridDim.x * blockDim.x) {
-    double w = pair_weight(s, k);
+    const double w = (k < n1) ? 1.0 : 0.5;
     double yv[TQ];
 #pragma unroll
-    for (int q = 0; q < TQ; ++q) yv[q] = (q < qn) ? w * Y[(int64_t)(q0 + q) * ldy + k] : 0.0;
+    for (int q = 0; q < TQ; ++q) yv[q] = w * Yq[q][k];
 #pragma unroll
     for (int p = 0; p < TP; ++p) {
-      double xv = (p < pn) ? X[(int64_t)(p0 + p) * ldx + k] : 0.0;
+      const double xv = Xp[p][k];
 #pragma unroll
       for (int q = 0; q < TQ; ++q) acc[p][q] = fma(xv, yv[q], acc[p][q]);
     }
   }
-  __shared__ double red[WD_BLOCK / 32];
+  __shared__ double red[WD_BLOCK / 32][TP * TQ];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int p = 0; p < pn; ++p) {
-    for (int q = 0; q < qn; ++q) {
-      double vsum = acc[p][q];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) vsum += __shfl_down_sync(0xffffffffu, vsum, off);
-      if (lane == 0) red[warp] = vsum;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double tsum = 0.0;
-        for (int w2 = 0; w2 < WD_BLOCK / 32; ++w2) tsum += red[w2];
-        work[((int64_t)blockIdx.x * np + (p0 + p)) * nq + (q0 + q)] = tsum;
-      }
-      __syncthreads();
+  for (int p = 0; p < TP; ++p)
+#pragma unroll
+    for (int q = 0; q < TQ; ++q) {
+      double v = acc[p][q];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) red[warp][p * TQ + q] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < TP * TQ) {
+    const int p = threadIdx.x / TQ, q = threadIdx.x % TQ;
+    if (p < pn && q < qn) {
+      double t = 0.0;
+      for (int w2 = 0; w2 < WD_BLOCK / 32; ++w2) t += red[w2][threadIdx.x];
+      work[((int64_t)blockIdx.x * np + (p0 + p)) * nq + (q0 + q)] = t;
     }
   }
 }
 
-__global__ void k_wdot_final(int nchunks, int np, int nq, const double* __restrict__ work, double* G, int ldg) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= np * nq) return;
-  int p = idx / nq, q = idx % nq;
-  double s = 0.0;
-  for (int c = 0; c < nchunks; ++c) s += work[((int64_t)c * np + p) * nq + q];
-  G[p * ldg + q] = s;
+// G[p][q] = sum over chunks + 1/2 sum over the doubles diagonal x_iiaa y_iiaa
+__global__ void k_wdot_final(VecShape s, int nchunks, int np, int nq, const double* __restrict__ work,
+                             const double* __restrict__ X, int64_t ldx, const double* __restrict__ Y, int64_t ldy,
+                             double* G, int ldg) {
+  const int pq = blockIdx.x;
+  const int p = pq / nq, q = pq % nq;
+  double sum = 0.0;
+  for (int c = threadIdx.x; c < nchunks; c += blockDim.x) sum += work[((int64_t)c * np + p) * nq + q];
+  const int64_t n1 = s.n1();
+  const int o = s.o, v = s.v;
+  const double* x = X + (int64_t)p * ldx + n1;
+  const double* y = Y + (int64_t)q * ldy + n1;
+  for (int ia = threadIdx.x; ia < o * v; ia += blockDim.x) {
+    const int i = ia / v, a = ia % v;
+    const int64_t e = (((int64_t)i * o + i) * v + a) * v + a;
+    sum = fma(0.5 * x[e], y[e], sum);
+  }
+  __shared__ double sh[128];
+  sh[threadIdx.x] = sum;
+  __syncthreads();
+  for (int off = 64; off > 0; off >>= 1) {
+    if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) G[p * ldg + q] = sh[0];
 }
 
 static int wdot_chunks() { return 152 * 2; }
@@ -427,11 +459,19 @@ int64_t wdot_work_size(int np, int nq) { return (int64_t)wdot_chunks() * np * nq
 void launch_wdot(const VecShape& s, const double* X, int64_t ldx, int np, const double* Y, int64_t ldy, int nq,
                  double* G, int ldg, double* work, cudaStream_t st) {
   if (np <= 0 || nq <= 0) return;
-  int nch = wdot_chunks();
-  dim3 grid(nch, (np + TP - 1) / TP, (nq + TQ - 1) / TQ);
+  const int nch = wdot_chunks();
   count_launches(2);
-  k_wdot_partial<<<grid, WD_BLOCK, 0, st>>>(s, X, ldx, np, Y, ldy, nq, work);
-  k_wdot_final<<<(np * nq + 127) / 128, 128, 0, st>>>(nch, np, nq, work, G, ldg);
+  if (np == 1 && nq == 1) {
+    k_wdot_partial<1, 1><<<dim3(nch, 1, 1), WD_BLOCK, 0, st>>>(s, X, ldx, np, Y, ldy, nq, work);
+  } else if (nq == 1) {
+    k_wdot_partial<4, 1><<<dim3(nch, (np + 3) / 4, 1), WD_BLOCK, 0, st>>>(s, X, ldx, np, Y, ldy, nq, work);
+  } else if (np == 1) {
+    k_wdot_partial<1, 4><<<dim3(nch, 1, (nq + 3) / 4), WD_BLOCK, 0, st>>>(s, X, ldx, np, Y, ldy, nq, work);
+  } else {
+    k_wdot_partial<4, 4><<<dim3(nch, (np + 3) / 4, (nq + 3) / 4), WD_BLOCK, 0, st>>>(s, X, ldx, np, Y, ldy, nq,
+                                                                                    work);
+  }
+  k_wdot_final<<<np * nq, 128, 0, st>>>(s, nch, np, nq, work, X, ldx, Y, ldy, G, ldg);
 }
 
 __global__ void k_lincomb(int64_t dim, const double* __restrict__ X, int64_t ldx, int np, const double* __restrict__ c,

@@ -4,19 +4,23 @@
 // sum of bf16 products: each FP64 operand is split into S bf16 slices
 // x = x_0 + x_1 (+ x_2) (x_0 = bf16(x), x_1 = bf16(x - x_0), ...), and the
 // products x_i y_j with i + j < S are accumulated in one FP32 TMEM accumulator
-// (S = 2: 3 products, ~16 significant bits; S = 3: 6 products, ~24 bits).
-// The slices live in a [S][rows][Kp] bf16 array (K padded to the 64-element
-// tile with zeros); a 3-D TMA map selects the slice with its third coordinate,
-// so the products are simply more K iterations of the same mainloop.
+// (S = 2: 3 products, ~16 significant bits; S = 3: 6 products, ~24 bits before
+// FP32 accumulation).  The slices live in a [S][rows][Kp] bf16 array (rows and
+// K padded with zeros to the tile sizes) written by one gather kernel straight
+// from the operand's strided FP64 layout; a 3-D TMA map selects the slice with
+// its third coordinate, so the products are simply more K iterations of the
+// same mainloop.
 //
 // Kernel: one 128 x BN output tile per CTA (BN = 64, 128 or 256), 4 warps.  Warp 0
 // lane 0 issues TMA loads into a 4- or 6-stage ring (mbarrier full/empty pairs),
 // warp 1 lane 0 issues tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulate,
-// 128 x BN x 16 per instruction) and commits each stage back to the producer; after the last
-// commit all four warps read the accumulator with tcgen05.ld (warp w owns TMEM
-// lanes 32w..32w+31) and add alpha * acc into the FP64 output.  Every mbarrier
-// wait is bounded; on timeout the kernel raises a device error flag, drains its
-// own copies and MMAs (bounded), frees TMEM and exits.
+// 128 x BN x 16 per instruction) and commits each stage back to the producer;
+// after the last commit all four warps read the accumulator with tcgen05.ld
+// (warp w owns TMEM lanes 32w..32w+31) and add alpha * acc into the FP64 output.
+// When the output has few tiles the K iterations are split over blockIdx.z and
+// the partial tiles are summed in FP64 by a second kernel.  Every mbarrier wait
+// is bounded; on timeout the kernel raises a device error flag, drains its own
+// copies and MMAs (bounded), frees TMEM and exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -48,15 +52,31 @@ constexpr int MAXPROD = 6;
 
 struct Params {
   int M, N;
-  int kt_per_prod;  // 64-wide K tiles per slice
+  int kt_per_prod;    // 64-wide K tiles per slice
   int nprod;
+  int it_per_split;   // K iterations per blockIdx.z
   int pa[MAXPROD], pb[MAXPROD];
-  double* C;
+  double* C;          // nsplit == 1: output
   long long sCm, sCn;
+  double* part;       // nsplit > 1: partial tiles [split][M][N]
   double alpha;
   int beta_zero;
   int* err;
+  // strided output (ostr != 0): element (m, n) lives at C + off(m; om) + off(n; on), where
+  // off(x; g) decomposes x row-major over g.ext and sums the coordinates times g.s0
+  int ostr;
+  Strided om, on;
 };
+
+__device__ __forceinline__ long long dim_offset(long long x, const Strided& g) {
+  long long off = 0;
+  for (int d = g.ndim - 1; d >= 0; --d) {
+    const long long e = g.ext[d];
+    off += (x % e) * g.s0[d];
+    x /= e;
+  }
+  return off;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -165,7 +185,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int iters = p.nprod * p.kt_per_prod;
+  const int total = p.nprod * p.kt_per_prod;
+  const int it0 = blockIdx.z * p.it_per_split;
+  const int it1 = min(total, it0 + p.it_per_split);
+  const int iters = max(0, it1 - it0);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -199,7 +222,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           ok = false;
           break;
         }
-        const int prod = it / p.kt_per_prod, kt = it % p.kt_per_prod;
+        const int g = it0 + it;
+        const int prod = g / p.kt_per_prod, kt = g % p.kt_per_prod;
         mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
         tma_load_3d(smem_u32(sA + s * A_BYTES), &ta, full0 + 8 * s, kt * BK, m0, p.pa[prod]);
         tma_load_3d(smem_u32(sB + s * B_BYTES), &tb, full0 + 8 * s, kt * BK, n0, p.pb[prod]);
@@ -241,13 +265,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncwarp();
   }
 
-  // epilogue: TMEM -> registers -> FP64 output
+  // epilogue: TMEM -> registers -> FP64 output (or FP64 partial tile)
   const bool ready = mbar_wait(done, 0, err);
   fence_after();
   if (!ready) atomicExch((int*)p.err, 1);
-  if (ready && !*err) {
+  if (ready && !*err && iters > 0) {
     const int row = m0 + warp * 32 + lane;
-    double* crow = p.C + (long long)row * p.sCm;
+    const bool split = (gridDim.z > 1);
+    const bool ostr = !split && p.ostr;
+    double* crow = split ? p.part + ((long long)blockIdx.z * p.M + row) * p.N
+                         : (ostr ? p.C + (row < p.M ? dim_offset(row, p.om) : 0) : p.C + (long long)row * p.sCm);
+    const long long cs = split ? 1 : p.sCn;
 #pragma unroll 1
     for (int c = 0; c < BN; c += 32) {
       uint32_t r[32];
@@ -257,13 +285,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int j = 0; j < 32; ++j) {
           const int n = n0 + c + j;
           if (n < p.N) {
-            double* dst = crow + (long long)n * p.sCn;
+            double* dst = crow + (ostr ? dim_offset(n, p.on) : (long long)n * cs);
             const double v = p.alpha * (double)__uint_as_float(r[j]);
-            *dst = p.beta_zero ? v : (*dst + v);
+            *dst = (split || p.beta_zero) ? v : (*dst + v);
           }
         }
       }
     }
+  } else if (ready && !*err && gridDim.z > 1) {
+    // an empty K range still owns its partial tile: write zeros
+    const int row = m0 + warp * 32 + lane;
+    if (row < p.M)
+      for (int n = n0; n < min(p.N, n0 + BN); ++n) p.part[((long long)blockIdx.z * p.M + row) * p.N + n] = 0.0;
   }
   fence_before();
   __syncthreads();
@@ -273,17 +306,41 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
-// FP64 -> S bf16 slices, dst[s][row][Kp] (K tail zero-filled by the caller).
-__global__ void k_split_pack(const double* __restrict__ src, int64_t rows, int64_t K, int64_t srow, int64_t sk, int S,
-                             int64_t Kp, int64_t plane, __nv_bfloat16* __restrict__ dst) {
-  const int64_t total = rows * K;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx / K, k = idx % K;
-    double x = src[r * srow + k * sk];
-    __nv_bfloat16* d = dst + r * Kp + k;
+// C[m, n] = sum_z part[z][m][n] (+ C[m, n] unless beta_zero); strided output as in Params
+__global__ void k_tc_reduce(int M, int N, int nsplit, const double* __restrict__ part, double* C, long long sCm,
+                            long long sCn, int beta_zero, int ostr, Strided om, Strided on) {
+  const long long tot = (long long)M * N;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+       idx += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < nsplit; ++z) s += part[(long long)z * tot + idx];
+    const long long m = idx / N, n = idx % N;
+    double* c = ostr ? C + dim_offset(m, om) + dim_offset(n, on) : C + m * sCm + n * sCn;
+    *c = beta_zero ? s : (*c + s);
+  }
+}
+
+// FP64 strided gather -> S bf16 slices, dst[s][row][Kp] with row-major (rows, K)
+// coordinates decomposed over the index space g (its leading dims index rows,
+// its trailing dims index K; g.s1 are the source strides).
+template <typename I>
+__global__ void k_split_pack(const double* __restrict__ src, Strided g, I K, I total, int S, int64_t Kp,
+                             int64_t plane, __nv_bfloat16* __restrict__ dst) {
+  for (I idx = (I)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (I)gridDim.x * blockDim.x) {
+    I r = idx;
+    int64_t off = 0;
+    for (int d = g.ndim - 1; d >= 0; --d) {
+      const I e = (I)g.ext[d];
+      const I c = r % e;
+      r /= e;
+      off += (int64_t)c * g.s1[d];
+    }
+    const I row = idx / K, k = idx % K;
+    double x = src[off];
+    __nv_bfloat16* dd = dst + (int64_t)row * Kp + k;
     for (int s = 0; s < S; ++s) {
       __nv_bfloat16 b = __double2bfloat16(x);
-      d[s * plane] = b;
+      dd[s * plane] = b;
       x -= (double)__bfloat162float(b);
     }
   }
@@ -323,11 +380,19 @@ static CUtensorMap make_map(const void* base, int64_t rows, int64_t Kp, int S, i
 
 struct Executor::CacheEntry {
   const double* src = nullptr;
-  int64_t rows = 0, rows_p = 0, K = 0, srow = 0, sk = 0;
+  Strided g;
+  int64_t rows_p = 0, K = 0;
   int S = 0;
   void* dev = nullptr;
   size_t bytes = 0;
 };
+
+static bool same_gather(const Strided& a, const Strided& b) {
+  if (a.ndim != b.ndim) return false;
+  for (int d = 0; d < a.ndim; ++d)
+    if (a.ext[d] != b.ext[d] || a.s1[d] != b.s1[d]) return false;
+  return true;
+}
 
 void Executor::clear_cache() {
   for (CacheEntry* e : cache_) {
@@ -335,6 +400,15 @@ void Executor::clear_cache() {
     delete e;
   }
   cache_.clear();
+  for (WPM& w : wpm_) {
+    if (w.plus) cudaFree(w.plus);
+    if (w.minus) cudaFree(w.minus);
+  }
+  wpm_.clear();
+  if (pairs_) {
+    cudaFree(pairs_);
+    pairs_ = nullptr;
+  }
   cache_bytes_ = 0;
   if (tc_err_) {
     cudaFree(tc_err_);
@@ -350,19 +424,23 @@ int Executor::tc_error() {
   return h;
 }
 
-// bf16 slices [S][rows][Kp] of an FP64 operand (cached when the operand is constant)
-// The slice planes have rows_p >= rows rows (a multiple of the TMA box) and
-// Kp >= K columns; the padding is zero so it adds nothing to the products.
-static __nv_bfloat16* make_slices(cudaStream_t st, const double* src, int64_t rows, int64_t rows_p, int64_t K,
-                                  int64_t srow, int64_t sk, int S, int64_t Kp) {
+// bf16 slices [S][rows_p][Kp] of an FP64 operand given as a strided gather over
+// (row dims..., K dims...); padding rows and columns are zero.
+static __nv_bfloat16* make_slices(cudaStream_t st, const double* src, const Strided& g, int64_t rows, int64_t rows_p,
+                                  int64_t K, int S, int64_t Kp) {
   size_t bytes = (size_t)S * rows_p * Kp * sizeof(__nv_bfloat16);
   void* p = nullptr;
   if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) throw std::runtime_error("tc operand allocation failed");
   if (Kp != K || rows_p != rows) cudaMemsetAsync(p, 0, bytes, st);
-  int64_t total = rows * K;
-  int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+  const int64_t total = rows * K;
+  const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
   count_launches(1);
-  tc::k_split_pack<<<grid, 256, 0, st>>>(src, rows, K, srow, sk, S, Kp, rows_p * Kp, (__nv_bfloat16*)p);
+  if (total < (int64_t(1) << 32))
+    tc::k_split_pack<uint32_t><<<grid, 256, 0, st>>>(src, g, (uint32_t)K, (uint32_t)total, S, Kp, rows_p * Kp,
+                                                     (__nv_bfloat16*)p);
+  else
+    tc::k_split_pack<uint64_t><<<grid, 256, 0, st>>>(src, g, (uint64_t)K, (uint64_t)total, S, Kp, rows_p * Kp,
+                                                     (__nv_bfloat16*)p);
   return (__nv_bfloat16*)p;
 }
 
@@ -377,22 +455,20 @@ static void launch_tc(dim3 grid, const CUtensorMap& ta, const CUtensorMap& tb, c
   tc::k_tc_gemm<BN><<<grid, tc::NTHREADS, tc::Cfg<BN>::SMEM_BYTES, st>>>(ta, tb, p);
 }
 
-bool Executor::tc_contract(int batch, int M, int N, int K, const double* A, int64_t sAb, int64_t sAm, int64_t sAk,
-                           const double* B, int64_t sBb, int64_t sBn, int64_t sBk, double* C, int64_t sCb,
-                           int64_t sCm, int64_t sCn, double alpha, double beta, bool a_const, bool b_const) {
-  (void)sAb;
-  (void)sBb;
-  (void)sCb;
-  if (batch != 1 || M < 1 || N < 1 || K < 1) return false;
+bool Executor::tc_contract(int M, int N, int K, const double* A, const Strided& Ag, const double* B,
+                           const Strided& Bg, double* C, int64_t sCm, int64_t sCn, double alpha, double beta,
+                           bool a_const, bool b_const, const Strided* om, const Strided* on) {
+  if (M < 1 || N < 1 || K < 1) return false;
   if (beta != 0.0 && beta != 1.0) return false;
+  Strided ag = Ag, bg = Bg;
   // the MMA tile is 128 rows of A by BN rows of B: put the longer side on A
   if (M < tc::BM && N > M) {
     std::swap(M, N);
     std::swap(A, B);
-    std::swap(sAm, sBn);
-    std::swap(sAk, sBk);
+    std::swap(ag, bg);
     std::swap(a_const, b_const);
     std::swap(sCm, sCn);
+    std::swap(om, on);
   }
   const int BN = (N > 128) ? 256 : (N > 64 ? 128 : 64);
   const int S = (splits_ >= 3) ? 3 : 2;
@@ -404,27 +480,42 @@ bool Executor::tc_contract(int batch, int M, int N, int K, const double* A, int6
     if (cudaMalloc(&tc_err_, sizeof(int)) != cudaSuccess) throw std::runtime_error("tc flag allocation failed");
     cudaMemsetAsync(tc_err_, 0, sizeof(int), st_);
   }
-  auto get = [&](const double* src, int64_t rows, int64_t rows_p, int64_t srow, int64_t sk, bool cst, bool& owned) {
+  auto get = [&](const double* src, const Strided& g, int64_t rows, int64_t rows_p, bool cst, bool& owned) {
     if (cst) {
       for (CacheEntry* e : cache_)
-        if (e->src == src && e->rows == rows && e->rows_p == rows_p && e->K == K && e->srow == srow &&
-            e->sk == sk && e->S == S) {
+        if (e->src == src && same_gather(e->g, g) && e->rows_p == rows_p && e->K == K && e->S == S) {
           owned = false;
           return (__nv_bfloat16*)e->dev;
         }
     }
-    __nv_bfloat16* p = make_slices(st_, src, rows, rows_p, K, srow, sk, S, Kp);
+    __nv_bfloat16* p = make_slices(st_, src, g, rows, rows_p, K, S, Kp);
     owned = !cst;
     if (cst) {
-      CacheEntry* e = new CacheEntry{src, rows, rows_p, (int64_t)K, srow, sk, S, p, (size_t)S * rows_p * Kp * 2};
+      CacheEntry* e = new CacheEntry{src, g, rows_p, (int64_t)K, S, p, (size_t)S * rows_p * Kp * 2};
       cache_.push_back(e);
       cache_bytes_ += e->bytes;
     }
     return p;
   };
   bool ownA = false, ownB = false;
-  __nv_bfloat16* a = get(A, M, Mp, sAm, sAk, a_const, ownA);
-  __nv_bfloat16* b = get(B, N, Np, sBn, sBk, b_const, ownB);
+  __nv_bfloat16* a = get(A, ag, M, Mp, a_const, ownA);
+  __nv_bfloat16* b = get(B, bg, N, Np, b_const, ownB);
+  tc_run(a, Mp, b, Np, K, Kp, S, M, N, C, sCm, sCn, alpha, beta, om, on);
+  if (ownA) cudaFreeAsync(a, st_);
+  if (ownB) cudaFreeAsync(b, st_);
+  return true;
+}
+
+void Executor::tc_run(const void* a, int64_t Mp, const void* b, int64_t Np, int K, int64_t Kp, int S, int M, int N,
+                      double* C, int64_t sCm, int64_t sCn, double alpha, double beta, const Strided* om,
+                      const Strided* on) {
+  (void)K;
+  const int BN = (N > 128) ? 256 : (N > 64 ? 128 : 64);
+  if (Np % BN != 0 || Mp % tc::BM != 0 || Np / BN > 65535) throw std::runtime_error("tc_run: bad padding");
+  if (!tc_err_) {
+    if (cudaMalloc(&tc_err_, sizeof(int)) != cudaSuccess) throw std::runtime_error("tc flag allocation failed");
+    cudaMemsetAsync(tc_err_, 0, sizeof(int), st_);
+  }
   CUtensorMap ta = tc::make_map(a, Mp, Kp, S, tc::BM);
   CUtensorMap tb = tc::make_map(b, Np, Kp, S, BN);
   tc::Params p;
@@ -439,13 +530,32 @@ bool Executor::tc_contract(int batch, int M, int N, int K, const double* A, int6
     p.pa[i] = (S == 2) ? pa3[i] : pa6[i];
     p.pb[i] = (S == 2) ? pb3[i] : pb6[i];
   }
+  const int iters = p.nprod * p.kt_per_prod;
+  const int64_t tiles = (Mp / tc::BM) * (Np / BN);
+  int nsplit = 1;
+  if (tiles < 148 && iters >= 32) nsplit = (int)std::min<int64_t>(std::min<int64_t>(296 / tiles, iters / 16), 64);
+  nsplit = std::max(nsplit, 1);
+  p.it_per_split = (iters + nsplit - 1) / nsplit;
+  nsplit = (iters + p.it_per_split - 1) / p.it_per_split;
   p.C = C;
   p.sCm = sCm;
   p.sCn = sCn;
+  p.part = nullptr;
   p.alpha = alpha;
   p.beta_zero = (beta == 0.0) ? 1 : 0;
   p.err = tc_err_;
-  dim3 grid((unsigned)(Mp / tc::BM), (unsigned)(Np / BN));
+  p.ostr = (om && on) ? 1 : 0;
+  if (p.ostr) {
+    p.om = *om;
+    p.on = *on;
+  } else {
+    p.om.ndim = p.on.ndim = 0;
+  }
+  if (nsplit > 1) {
+    if (cudaMallocAsync((void**)&p.part, (size_t)nsplit * M * N * sizeof(double), st_) != cudaSuccess)
+      throw std::runtime_error("tc split workspace allocation failed");
+  }
+  dim3 grid((unsigned)(Mp / tc::BM), (unsigned)(Np / BN), (unsigned)nsplit);
   last_tc_issued = 2.0 * (double)Mp * (double)Np * (double)Kp * p.nprod;
   if (BN == 256)
     launch_tc<256>(grid, ta, tb, p, st_);
@@ -453,11 +563,15 @@ bool Executor::tc_contract(int batch, int M, int N, int K, const double* A, int6
     launch_tc<128>(grid, ta, tb, p, st_);
   else
     launch_tc<64>(grid, ta, tb, p, st_);
+  if (nsplit > 1) {
+    const long long tot = (long long)M * N;
+    count_launches(1);
+    tc::k_tc_reduce<<<(int)std::min<long long>((tot + 255) / 256, 152 * 16), 256, 0, st_>>>(
+        M, N, nsplit, p.part, C, sCm, sCn, p.beta_zero, p.ostr, p.om, p.on);
+    cudaFreeAsync(p.part, st_);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw std::runtime_error(std::string("tc gemm launch: ") + cudaGetErrorString(e));
-  if (ownA) cudaFreeAsync(a, st_);
-  if (ownB) cudaFreeAsync(b, st_);
-  return true;
 }
 
 }  // namespace ccsd
