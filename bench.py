@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--splits", type=int, default=3)
     ap.add_argument("--amplitudes", choices=["solve", "synthetic"], default="solve",
                     help="converge the ground state in set-up, or use seeded synthetic amplitudes")
+    ap.add_argument("--ttc", choices=["mixed", "fp64", "both"], default=None,
+                    help="instead of transform throughput, time create -> ground -> EOM (2 roots) -> couplings")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -330,8 +332,55 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(out), flush=True)
 
 
+def run_ttc(args):
+    """Time-to-converged coupling: wall time from ccsd_create through the
+    derivative couplings F_12, F_01, F_20 along (h1, B1), per precision form, at
+    the same convergence thresholds (1e-10 residual, 1e-8 EOM, 1e-9 linear)."""
+    import torch
+    from paper_2301_13264_gb300 import binding as B
+    from paper_2301_13264_gb300.synth import workload
+
+    H = workload(args.workload)
+    forms = ["mixed", "fp64"] if args.ttc == "both" else [args.ttc]
+    out = {"metric": "time-to-converged coupling", "unit": "s", "higher_is_better": False,
+           "workload": f"{args.workload} o={H.o} v={H.v} naux={H.naux}", "pairs": [[1, 2], [0, 1], [2, 0]],
+           "forms": {}}
+    for form in forms:
+        prec = B.PREC_MIXED if form == "mixed" else B.PREC_FP64
+        opt = B.ccsd_default_options(precision=prec, splits=args.splits, tol_res=1e-10, tol_eom=1e-8,
+                                     tol_lin=1e-9, max_iter=200, refine=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = B.ccsd_create(H.eps, H.h, H.B, H.o, H.v, H.naux, opt)
+        e, it_g = B.ccsd_solve_ground(h)
+        t_g = time.perf_counter() - t0
+        print(f"[ttc {form}] ground {t_g:.1f}s {it_g} iterations E={e:.12f}", file=sys.stderr, flush=True)
+        w, it_r = B.eom_solve_right(h, 2)
+        print(f"[ttc {form}] right EOM {time.perf_counter() - t0:.1f}s {it_r} iterations {w}", file=sys.stderr,
+              flush=True)
+        wl, it_l = B.eom_solve_left(h, 2)
+        t_e = time.perf_counter() - t0
+        F = [B.ccsd_derivative_coupling(h, k, l, 1, H.h1, H.B1)[0] for k, l in out["pairs"]]
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        out["forms"][form] = {"seconds": t, "ground_s": t_g, "eom_s": t_e - t_g, "couplings_s": t - t_e,
+                              "e_ccsd": e, "omega": w, "F": F, "iters": [it_g, it_r, it_l],
+                              "stats": B.ccsd_stats(h)}
+        B.ccsd_destroy(h)
+    if len(forms) == 2:
+        m, f = out["forms"]["mixed"], out["forms"]["fp64"]
+        out["speedup"] = f["seconds"] / m["seconds"]
+        out["energy_diff"] = abs(m["e_ccsd"] - f["e_ccsd"])
+        out["omega_diff"] = max(abs(a - b) for a, b in zip(m["omega"], f["omega"]))
+        out["coupling_rel_diff"] = max(abs(a - b) / abs(b) for a, b in zip(m["F"], f["F"]))
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.ttc:
+        run_ttc(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

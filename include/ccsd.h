@@ -74,6 +74,9 @@ typedef struct {
   int guess;            /* CCSD_GUESS_MP2 */
   void* stream;         /* cudaStream_t, 0 = default */
   double tc_min_flops;  /* mixed mode: contractions below this many flops stay FP64 */
+  int refine;           /* mixed mode: 1 = refine every solve to the FP64 tolerances above (FP64 residuals
+                           with mixed-precision correction solves); 0 = stop at the mixed-precision floor */
+  double tol_switch;    /* mixed mode with refine: residual level at which the FP64 refinement starts */
 } ccsd_options;
 
 /* Fill *opt with defaults (FP64, tol_res 1e-10, tol_eom 1e-7, tol_lin 1e-9, ...). */
@@ -135,6 +138,35 @@ ccsd_status ccsd_coupling_densities(ccsd_handle h, int k, int l, double* D, doub
 /* F[d] = F_kl^x along ndir directions: dh[d][n*n], dB[d][naux*n*n]. */
 ccsd_status ccsd_derivative_coupling(ccsd_handle h, int k, int l, int ndir, const double* dh, const double* dB,
                                      double* F);
+
+/* ---- learned initial guess for the doubles amplitudes ---------------------
+ * A 3 -> 128 -> 128 -> 1 MLP (tanh hidden layers) maps per-element features
+ * x_ijab = (t_MP2, D, |(ia|jb)|), t_MP2 = -(ia|jb)/D, D = e_a + e_b - e_i - e_j, to
+ * the correction t_CCSD - t_MP2 (an extension to the paper's method: a starting
+ * point for the amplitude equations, which does not change the converged result).
+ * A model is CCSD_MLP_PARAMS floats: W1[128][3], b1[128], W2[128][128], b2[128],
+ * w3[128], b3, then feature mean[3], feature scale[3], target scale.  Training
+ * (Adam, mean squared error) and inference run in the library's kernels; inference
+ * uses the weights rounded to bf16 with FP32 accumulation.  Arrays may be host or
+ * device memory. */
+#define CCSD_MLP_PARAMS 17160
+/* Train from scratch on n rows X[n][3], T[n] for `steps` minibatches of `batch`
+ * rows (learning rate lr, cosine decay); model_out[CCSD_MLP_PARAMS]; *final_loss =
+ * mean squared error over the training rows in units of the target scale. */
+ccsd_status ccsd_mlp_train(const float* X, const float* T, long long n, int steps, int batch, float lr,
+                           unsigned long long seed, float* model_out, float* final_loss);
+/* out[n] = model predictions for X[n][3]. */
+ccsd_status ccsd_mlp_predict(const float* model, const float* X, long long n, float* out);
+/* grad[CCSD_MLP_PARAMS - 7] = gradient of the mean squared error (normalised target
+ * units) over all n rows with respect to the trainable weights; *loss = that error.
+ * FP32 weights (no bf16 rounding). */
+ccsd_status ccsd_mlp_gradient(const float* model, const float* X, const float* T, long long n, float* grad,
+                              float* loss);
+/* X[o*o*v*v][3] = the features of the handle's Hamiltonian, doubles in [i][j][a][b] order. */
+ccsd_status ccsd_guess_features(ccsd_handle h, float* X);
+/* Use `model` for the starting doubles of the next ccsd_solve_ground (NULL: the
+ * MP2-type start).  The model is copied. */
+ccsd_status ccsd_set_guess_model(ccsd_handle h, const float* model);
 
 /* Allocation-free variant of ccsd_derivative_coupling (the paper has no
  * counterpart; this is a service for callers that cannot allocate device

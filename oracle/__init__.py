@@ -19,4 +19,6 @@ solvers   : ground-state amplitudes, ground-state multipliers, EOM left/right
             states, biorthonormalisation, the coupling multipliers and the
             derivative coupling of Eq. (NAC_NC), plus a finite-difference
             evaluation of the definition Eq. (nac).
+mlp       : the learned doubles guess (features, network, gradients of its
+            training loss), an extension outside the paper's method.
 """

@@ -14,9 +14,14 @@ from .binding import (  # noqa: F401
     ccsd_destroy,
     ccsd_get_amplitudes,
     ccsd_get_states,
+    ccsd_guess_features,
     ccsd_jacobian_transform,
+    ccsd_mlp_gradient,
+    ccsd_mlp_predict,
+    ccsd_mlp_train,
     ccsd_residual,
     ccsd_set_amplitudes,
+    ccsd_set_guess_model,
     ccsd_solve_ground,
     ccsd_stats,
     eom_solve_left,

@@ -36,6 +36,8 @@ class Options(ctypes.Structure):
         ("guess", ctypes.c_int),
         ("stream", ctypes.c_void_p),
         ("tc_min_flops", ctypes.c_double),
+        ("refine", ctypes.c_int),
+        ("tol_switch", ctypes.c_double),
     ]
 
 
@@ -252,3 +254,71 @@ def ccsd_describe_program(which: str) -> str:
 
 def vector_dim(o: int, v: int) -> int:
     return o * v + o * o * v * v
+
+
+# ---- learned doubles guess -------------------------------------------------
+
+MLP_PARAMS = 17160
+MLP_TRAINABLE = MLP_PARAMS - 7
+
+
+def _fptr(x, n=None):
+    """Raw pointer of a contiguous float32 numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float32 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous float32")
+        if n is not None and x.size < n:
+            raise ValueError(f"array needs at least {n} elements")
+        return ctypes.c_void_p(x.ctypes.data)
+    import torch
+    if x.dtype != torch.float32 or not x.is_contiguous():
+        raise ValueError("tensors must be contiguous float32")
+    if n is not None and x.numel() < n:
+        raise ValueError(f"tensor needs at least {n} elements")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _mlp_fn(name, argtypes):
+    f = getattr(lib(), name)
+    if not getattr(f, "argtypes", None):
+        f.argtypes = argtypes
+        f.restype = ctypes.c_int
+    return f
+
+
+def ccsd_mlp_train(X, T, steps, batch=4096, lr=2e-3, seed=0):
+    """Train a model on rows X[n, 3] -> T[n]; returns (model float32[MLP_PARAMS], final loss)."""
+    n = T.shape[0]
+    model = np.zeros(MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    f = _mlp_fn("ccsd_mlp_train", [_P, _P, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                   ctypes.c_ulonglong, _P, ctypes.POINTER(ctypes.c_float)])
+    _check(None, f(_fptr(X, 3 * n), _fptr(T, n), n, steps, batch, lr, seed, _fptr(model), ctypes.byref(loss)))
+    return model, loss.value
+
+
+def ccsd_mlp_predict(model, X, out):
+    n = out.shape[0]
+    f = _mlp_fn("ccsd_mlp_predict", [_P, _P, ctypes.c_longlong, _P])
+    _check(None, f(_fptr(model, MLP_PARAMS), _fptr(X, 3 * n), n, _fptr(out, n)))
+
+
+def ccsd_mlp_gradient(model, X, T):
+    """(loss, gradient float32[MLP_TRAINABLE]) of the training loss over all rows."""
+    n = T.shape[0]
+    grad = np.zeros(MLP_TRAINABLE, dtype=np.float32)
+    loss = ctypes.c_float()
+    f = _mlp_fn("ccsd_mlp_gradient", [_P, _P, _P, ctypes.c_longlong, _P, ctypes.POINTER(ctypes.c_float)])
+    _check(None, f(_fptr(model, MLP_PARAMS), _fptr(X, 3 * n), _fptr(T, n), n, _fptr(grad), ctypes.byref(loss)))
+    return loss.value, grad
+
+
+def ccsd_guess_features(h, X):
+    """Fill X (float32, o*o*v*v*3 elements, [i][j][a][b][3]) with the handle's features."""
+    f = _mlp_fn("ccsd_guess_features", [_P, _P])
+    _check(h, f(h, _fptr(X)))
+
+
+def ccsd_set_guess_model(h, model):
+    f = _mlp_fn("ccsd_set_guess_model", [_P, _P])
+    _check(h, f(h, None if model is None else _fptr(model, MLP_PARAMS)))

@@ -17,8 +17,11 @@
 #include "../../include/ccsd.h"
 #include "exec.h"
 #include "kernels.cuh"
+#include "mlp.h"
 #include "programs.h"
 #include "small_linalg.h"
+
+static_assert(ccsd::mlp::kParams == CCSD_MLP_PARAMS, "model size");
 
 using namespace ccsd;
 
@@ -87,6 +90,7 @@ struct ccsd_ctx {
   int dens_k = -1, dens_l = -1;
   DevBuf Dd, Zd;
   long long prof_launch0 = 0;
+  DevBuf guess_model;  // MLP model (floats) for the starting doubles, or empty
 };
 
 namespace {
@@ -257,6 +261,61 @@ struct Diis {
   }
 };
 
+// Sets the executor's precision for a scope.
+struct PrecScope {
+  ccsd_ctx* c;
+  int old;
+  PrecScope(ccsd_ctx* c_, int p) : c(c_), old(c_->ex->precision()) { c->ex->set_precision(p, c->opt.splits); }
+  ~PrecScope() { c->ex->set_precision(old, c->opt.splits); }
+};
+
+bool refining(ccsd_ctx* c) { return c->opt.precision == CCSD_PREC_MIXED && c->opt.refine; }
+
+// Solve A x = -rhs by preconditioned Jacobi + DIIS (right transforms); x holds the guess on entry
+int solve_right_linear(ccsd_ctx* c, const double* rhs, double* x, double tol, int maxit) {
+  DevBuf res(c->dim), xn(c->dim);
+  Diis diis(c, c->opt.diis_dim);
+  for (int it = 1; it <= maxit; ++it) {
+    right_block(c, x, res.p, 1);
+    launch_axpby(c->dim, 1.0, rhs, 1.0, res.p, c->st);
+    double err = maxabs(c, res.p, c->dim);
+    if (!std::isfinite(err)) throw Err(CCSD_ERR_NOT_CONVERGED, "linear equations diverged");
+    if (err < tol) return it;
+    launch_precond(c->vs, c->eps.p, res.p, xn.p, 0.0, c->st);
+    launch_axpby(c->dim, 1.0, x, -1.0, xn.p, c->st);
+    diis.step(xn.p, res.p, x);
+  }
+  return maxit;
+}
+
+int solve_left_linear(ccsd_ctx* c, const double* rhs, double* x, double tol);
+
+// x^T A = -rhs^T to the FP64 tolerance: in mixed mode with refinement the
+// equations are first solved in mixed precision to tol_switch, then corrected:
+// rho = rhs + A_64^T x (FP64 left transform), A^T d = -rho solved in mixed
+// precision to a fraction of |rho|, x += d, until max |rho| < tol.
+int solve_left_refined(ccsd_ctx* c, const double* rhs, double* x, double tol) {
+  if (!refining(c)) return solve_left_linear(c, rhs, x, tol);
+  int it = solve_left_linear(c, rhs, x, std::max(tol, c->opt.tol_switch));
+  DevBuf rho(c->dim), d(c->dim);
+  for (int outer = 0; outer < 20; ++outer) {
+    {
+      PrecScope fp64(c, CCSD_PREC_FP64);
+      left_block(c, x, rho.p, 1);
+    }
+    launch_axpby(c->dim, 1.0, rhs, 1.0, rho.p, c->st);
+    ++it;
+    double err = maxabs(c, rho.p, c->dim);
+    if (!std::isfinite(err)) throw Err(CCSD_ERR_NOT_CONVERGED, "refinement diverged");
+    if (err < tol) return it;
+    launch_precond(c->vs, c->eps.p, rho.p, d.p, 0.0, c->st);
+    launch_axpby(c->dim, 0.0, d.p, -1.0, d.p, c->st);
+    it += solve_left_linear(c, rho.p, d.p, std::max(1e-3 * err, 0.1 * tol));
+    launch_axpby(c->dim, 1.0, d.p, 1.0, x, c->st);
+  }
+  throw Err(CCSD_ERR_NOT_CONVERGED, "FP64 refinement of the linear equations did not converge");
+}
+
 // Solve x^T A = -rhs^T by preconditioned Jacobi + DIIS; x holds the guess on entry
 int solve_left_linear(ccsd_ctx* c, const double* rhs, double* x, double tol) {
   DevBuf res(c->dim), xn(c->dim);
@@ -277,7 +336,8 @@ int solve_left_linear(ccsd_ctx* c, const double* rhs, double* x, double tol) {
 // ---------------------------------------------------------------------------
 // Davidson for the lowest nroots of A (side 0) or A^T (side 1)
 // ---------------------------------------------------------------------------
-int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std::vector<std::unique_ptr<DevBuf>>& out) {
+int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std::vector<std::unique_ptr<DevBuf>>& out,
+             double tol, const std::vector<std::unique_ptr<DevBuf>>* init = nullptr) {
   const int64_t dim = c->dim;
   const int maxsub = std::max(c->opt.davidson_max_sub, 3 * nroots);
   const int block = std::max(1, std::min(c->opt.davidson_block, 16));
@@ -326,8 +386,14 @@ int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std:
     }
     return kept;
   };
-  // guesses: singles unit vectors of the lowest orbital-energy differences
-  {
+  // guesses: the given vectors, else singles unit vectors of the lowest orbital-energy differences
+  if (init && (int)init->size() >= nroots) {
+    for (int g = 0; g < nroots; ++g)
+      CUDA_OK(cudaMemcpyAsync(V.p + g * dim, (*init)[g]->p, dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    int kept = orthonormalize(nroots);
+    apply(0, kept);
+    m = kept;
+  } else {
     std::vector<double> eps(c->n);
     CUDA_OK(cudaMemcpy(eps.data(), c->eps.p, c->n * sizeof(double), cudaMemcpyDeviceToHost));
     std::vector<std::pair<double, int>> d1;
@@ -346,6 +412,7 @@ int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std:
     m = kept;
   }
   DevBuf X(nroots * dim), AX(nroots * dim), Rz(nroots * dim);
+  int complex_run = 0;
   for (int it = 1; it <= c->opt.max_iter; ++it) {
     std::vector<double> G(m * m);
     for (int i = 0; i < m; ++i)
@@ -355,14 +422,41 @@ int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std:
     if ((int)ev.size() < nroots) throw Err(CCSD_ERR_NOT_CONVERGED, "subspace too small");
     double scale = 0.0;
     for (auto& e : ev) scale = std::max(scale, std::abs(e));
-    for (int k = 0; k < nroots; ++k)
-      if (std::fabs(ev[k].imag()) > 1e-9 * std::max(scale, 1.0))
-        throw Err(CCSD_ERR_COMPLEX_ROOT, "complex eigenvalue among the wanted roots");
+    // A complex pair a +- ib among the wanted subspace eigenvalues is usually
+    // transient (a small subspace of a non-symmetric matrix); the pair's real 2-D
+    // invariant subspace is then spanned by u (inverse iteration at a) and (G - a)u,
+    // which serve as the two Ritz-like vectors with shift a.  A pair that survives
+    // many expansions is reported.
+    bool cplx = false;
+    for (int k = 0; k < nroots; ++k) cplx |= std::fabs(ev[k].imag()) > 1e-9 * std::max(scale, 1.0);
+    complex_run = cplx ? complex_run + 1 : 0;
+    if (complex_run > 12) throw Err(CCSD_ERR_COMPLEX_ROOT, "complex eigenvalue among the wanted roots");
     std::vector<double> U(m * nroots);
     omega.assign(nroots, 0.0);
+    std::vector<double> prev;
     for (int k = 0; k < nroots; ++k) {
       omega[k] = ev[k].real();
-      std::vector<double> u = eigenvector(m, G, omega[k]);
+      const bool is_c = std::fabs(ev[k].imag()) > 1e-9 * std::max(scale, 1.0);
+      const bool partner = is_c && k > 0 && !prev.empty() && std::fabs(ev[k].real() - ev[k - 1].real()) <=
+                                                                 1e-12 * std::max(scale, 1.0);
+      std::vector<double> u(m);
+      if (partner) {  // (G - a) u_prev, normalised
+        double nn = 0.0;
+        for (int i = 0; i < m; ++i) {
+          double s = -omega[k] * prev[i];
+          for (int j = 0; j < m; ++j) s += G[i * m + j] * prev[j];
+          u[i] = s;
+          nn += s * s;
+        }
+        for (int i = 0; i < m; ++i) u[i] /= std::sqrt(std::max(nn, 1e-300));
+        prev.clear();
+      } else {
+        u = eigenvector(m, G, omega[k]);
+        if (is_c)
+          prev = u;
+        else
+          prev.clear();
+      }
       for (int i = 0; i < m; ++i) U[i * nroots + k] = u[i];
     }
     lincomb(c, V.p, dim, m, U, X.p, dim, nroots, false);
@@ -379,8 +473,8 @@ int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std:
     }
     std::vector<double> rn = gram(c, Rz.p, dim, nroots, Rz.p, dim, nroots);
     for (int k = 0; k < nroots; ++k)
-      if (std::sqrt(std::max(rn[k * nroots + k], 0.0)) > c->opt.tol_eom) todo.push_back(k);
-    if (todo.empty()) {
+      if (std::sqrt(std::max(rn[k * nroots + k], 0.0)) > tol) todo.push_back(k);
+    if (todo.empty() && !cplx) {
       out.clear();
       for (int k = 0; k < nroots; ++k) {
         out.emplace_back(new DevBuf(dim));
@@ -407,6 +501,19 @@ int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std:
     m += kept;
   }
   throw Err(CCSD_ERR_NOT_CONVERGED, "Davidson not converged");
+}
+
+// Davidson to tol_eom; in mixed mode with refinement the mixed-precision solution
+// (to 10 tol_switch) seeds an FP64 continuation, which needs only a few transforms.
+int davidson_refined(ccsd_ctx* c, int side, int nroots, std::vector<double>& w,
+                     std::vector<std::unique_ptr<DevBuf>>& out,
+                     const std::vector<std::unique_ptr<DevBuf>>* init = nullptr) {
+  if (!refining(c)) return davidson(c, side, nroots, w, out, c->opt.tol_eom, init);
+  std::vector<std::unique_ptr<DevBuf>> mixed;
+  int it = davidson(c, side, nroots, w, mixed, std::max(c->opt.tol_eom, 10.0 * c->opt.tol_switch), init);
+  PrecScope fp64(c, CCSD_PREC_FP64);
+  it += davidson(c, side, nroots, w, out, c->opt.tol_eom, &mixed);
+  return it;
 }
 
 // normalise R to unit packed norm, largest-magnitude component positive
@@ -481,6 +588,7 @@ void compute_densities(ccsd_ctx* c, int k, int l) {
     ex.bind(P.eZ2, Wz.p + c->n1);
     ex.bind(P.eH, c->Dd.p);
     ex.bind(P.eB, c->Zd.p);
+    PrecScope p(c, refining(c) ? CCSD_PREC_FP64 : ex.precision());
     ex.run(P.dens0);
   } else {
     double dw = omega_of(c, l) - omega_of(c, k);
@@ -493,12 +601,15 @@ void compute_densities(ccsd_ctx* c, int k, int l) {
     launch_axpby(dim, 1.0 / dw, left_vec(c, k), 0.0, gam.p, c->st);
     // t-eta = <L_k|tau|R_l> + d^2(g0 E + gamma.Omega)/dt^2 R_l
     launch_tau_expectation(c->vs, r0, left_vec(c, k), Rl, teta.p, c->st);
-    hess_right(c, g0, gam.p, Rl, hv.p);
+    {
+      PrecScope p(c, refining(c) ? CCSD_PREC_FP64 : ex.precision());
+      hess_right(c, g0, gam.p, Rl, hv.p);
+    }
     launch_axpby(dim, 1.0, hv.p, 1.0, teta.p, c->st);
     // zeta^T A = -t-eta^T (Eq. amplituderelax)
     launch_precond(c->vs, c->eps.p, teta.p, zeta.p, 0.0, c->st);
     launch_axpby(dim, 0.0, zeta.p, -1.0, zeta.p, c->st);
-    solve_left_linear(c, teta.p, zeta.p, c->opt.tol_lin);
+    solve_left_refined(c, teta.p, zeta.p, c->opt.tol_lin);
     launch_weight(c->vs, zeta.p, Wz.p, 1, dim, c->st);
     launch_weight(c->vs, gam.p, Wg.p, 1, dim, c->st);
     CUDA_OK(cudaMemcpyAsync(s0.p, &g0, sizeof(double), cudaMemcpyHostToDevice, c->st));
@@ -513,6 +624,7 @@ void compute_densities(ccsd_ctx* c, int k, int l) {
     ex.bind(P.dR2, const_cast<double*>(Rl) + c->n1);
     ex.bind(P.dH, c->Dd.p);
     ex.bind(P.dB, c->Zd.p);
+    PrecScope p(c, refining(c) ? CCSD_PREC_FP64 : ex.precision());
     ex.run(P.dens1);
   }
   sync(c);
@@ -541,6 +653,8 @@ void ccsd_default_options(ccsd_options* opt) {
   opt->guess = CCSD_GUESS_MP2;
   opt->stream = nullptr;
   opt->tc_min_flops = 2.0e9;
+  opt->refine = 1;
+  opt->tol_switch = 1e-6;
 }
 
 const char* ccsd_strerror(ccsd_status s) {
@@ -637,7 +751,14 @@ ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int
     ex.ladder_w_ = cp.g.id("W");
     ex.const_tensors = {cp.h, cp.B, cp.ones_o};
     for (const Op& op : cp.fwd_const) ex.const_tensors.insert(op.out.t);
-    ex.run(cp.fwd_const);
+    {
+      // under FP64 refinement the Hamiltonian-only intermediates are built in FP64,
+      // so that the refined equations are exactly the FP64 ones
+      const int p0 = ex.precision();
+      if (refining(c)) ex.set_precision(CCSD_PREC_FP64, c->opt.splits);
+      ex.run(cp.fwd_const);
+      ex.set_precision(p0, c->opt.splits);
+    }
     sync(c);
   });
   if (s != CCSD_OK) {
@@ -678,26 +799,72 @@ ccsd_status ccsd_solve_ground(ccsd_handle c, double* e_ccsd, int* iters) {
     c->dens_k = c->dens_l = -1;
     int it = 1;
     double e = 0.0;
+    const bool refine = refining(c);
+    // mixed phase stops at tol_switch (or when it stalls); refinement follows
+    const double tol1 = refine ? std::max(c->opt.tol_res, c->opt.tol_switch) : c->opt.tol_res;
+    double best = 1e300;
+    int since_best = 0;
     for (;; ++it) {
       if (it > c->opt.max_iter) throw Err(CCSD_ERR_NOT_CONVERGED, "ground state not converged");
       e = forward(c, c->t.p, om.p);
       double err = maxabs(c, om.p, dim);
       if (!std::isfinite(err) || !std::isfinite(e)) throw Err(CCSD_ERR_NOT_CONVERGED, "ground state diverged");
-      if (err < c->opt.tol_res) break;
+      if (err < tol1) break;
+      if (err < 0.5 * best) {
+        best = err;
+        since_best = 0;
+      } else if (refine && ++since_best >= 6 && err < 1e3 * tol1) {
+        break;  // at the mixed-precision floor
+      }
       launch_precond(c->vs, c->eps.p, om.p, tn.p, 0.0, c->st);
       launch_axpby(dim, 1.0, c->t.p, -1.0, tn.p, c->st);  // tn = t - Omega/D
+      if (it == 1 && c->guess_model.p) {
+        // learned start: t2 = t_MP2 + MLP(features) (t_MP2 = -Omega_2(0)/D is tn's doubles)
+        const int64_t n2 = dim - c->n1;
+        DevBuf X((n2 * 3 + 1) / 2), delta((n2 + 1) / 2);
+        const double* gov = c->ex->ptr(c->P.cp.g.id("Govov"));
+        mlp::features(gov, c->eps.p, c->o, c->v, (float*)X.p, c->st);
+        mlp::predict((const float*)c->guess_model.p, (const float*)X.p, n2, (float*)delta.p, c->st);
+        mlp::add_delta(tn.p + c->n1, (const float*)delta.p, n2, c->st);
+        sync(c);
+      }
       diis.step(tn.p, om.p, c->t.p);
       c->cache_at_t = false;
     }
+    if (refine) {
+      // Newton-type defect correction: Omega_64(t) in FP64, A d = -Omega_64 solved
+      // with mixed-precision right transforms at t, t += d
+      DevBuf d(dim);
+      c->have_ground = true;  // the transforms below need the amplitudes in place
+      for (int outer = 0;; ++outer) {
+        if (outer >= 20) throw Err(CCSD_ERR_NOT_CONVERGED, "FP64 refinement of the ground state did not converge");
+        {
+          PrecScope fp64(c, CCSD_PREC_FP64);
+          e = forward(c, c->t.p, om.p);
+        }
+        ++it;
+        double err = maxabs(c, om.p, dim);
+        if (!std::isfinite(err)) throw Err(CCSD_ERR_NOT_CONVERGED, "ground state refinement diverged");
+        if (err < c->opt.tol_res) break;
+        launch_precond(c->vs, c->eps.p, om.p, d.p, 0.0, c->st);
+        launch_axpby(dim, 0.0, d.p, -1.0, d.p, c->st);
+        it += solve_right_linear(c, om.p, d.p, std::max(1e-3 * err, 0.1 * c->opt.tol_res), c->opt.max_iter);
+        launch_axpby(dim, 1.0, d.p, 1.0, c->t.p, c->st);
+        c->cache_at_t = false;
+      }
+    }
     c->e_ccsd = e;
     c->have_ground = true;
-    // eta = dE/dt and the ground-state multipliers lambda^T A = -eta^T
+    // eta = dE/dt (FP64) and the ground-state multipliers lambda^T A = -eta^T
     DevBuf zero(dim);
     CUDA_OK(cudaMemsetAsync(zero.p, 0, dim * sizeof(double), c->st));
-    left_block(c, zero.p, c->eta.p, 1, 1.0);
+    {
+      PrecScope p(c, refine ? CCSD_PREC_FP64 : c->ex->precision());
+      left_block(c, zero.p, c->eta.p, 1, 1.0);
+    }
     launch_precond(c->vs, c->eps.p, c->eta.p, c->lam.p, 0.0, c->st);
     launch_axpby(dim, 0.0, c->lam.p, -1.0, c->lam.p, c->st);
-    solve_left_linear(c, c->eta.p, c->lam.p, c->opt.tol_lin);
+    solve_left_refined(c, c->eta.p, c->lam.p, c->opt.tol_lin);
     if (e_ccsd) *e_ccsd = e;
     if (iters) *iters = it;
   });
@@ -708,7 +875,7 @@ ccsd_status eom_solve_right(ccsd_handle c, int nroots, double* omega, int* iters
     if (nroots < 1 || nroots > c->n1) throw Err(CCSD_ERR_ARG, "bad nroots");
     if (!c->have_ground) throw Err(CCSD_ERR_STATE, "ground state not solved");
     std::vector<double> w;
-    int it = davidson(c, 0, nroots, w, c->R);
+    int it = davidson_refined(c, 0, nroots, w, c->R);
     c->omega = w;
     c->r0.assign(nroots, 0.0);
     for (int k = 0; k < nroots; ++k) {
@@ -730,7 +897,8 @@ ccsd_status eom_solve_left(ccsd_handle c, int nroots, double* omega, int* iters)
     if (nroots != (int)c->omega.size()) throw Err(CCSD_ERR_ARG, "nroots differs from the right solve");
     std::vector<double> w;
     std::vector<std::unique_ptr<DevBuf>> Lr;
-    int it = davidson(c, 1, nroots, w, Lr);
+    // the right eigenvectors start the left solve: same roots, close vectors
+    int it = davidson_refined(c, 1, nroots, w, Lr, &c->R);
     for (int k = 0; k < nroots; ++k)
       if (std::fabs(w[k] - c->omega[k]) > 1e-5 * std::max(1.0, std::fabs(c->omega[k])))
         throw Err(CCSD_ERR_NOT_CONVERGED, "left and right roots differ");
@@ -797,13 +965,16 @@ ccsd_status ccsd_set_amplitudes(ccsd_handle c, const double* t, const double* la
     c->have_ground = true;
     DevBuf zero(dim);
     CUDA_OK(cudaMemsetAsync(zero.p, 0, dim * sizeof(double), c->st));
-    left_block(c, zero.p, c->eta.p, 1, 1.0);
+    {
+      PrecScope p(c, refining(c) ? CCSD_PREC_FP64 : c->ex->precision());
+      left_block(c, zero.p, c->eta.p, 1, 1.0);
+    }
     if (lambda) {
       CUDA_OK(cudaMemcpyAsync(c->lam.p, lambda, dim * sizeof(double), cudaMemcpyDefault, c->st));
     } else {
       launch_precond(c->vs, c->eps.p, c->eta.p, c->lam.p, 0.0, c->st);
       launch_axpby(dim, 0.0, c->lam.p, -1.0, c->lam.p, c->st);
-      solve_left_linear(c, c->eta.p, c->lam.p, c->opt.tol_lin);
+      solve_left_refined(c, c->eta.p, c->lam.p, c->opt.tol_lin);
     }
     sync(c);
     if (e) *e = en;
@@ -903,7 +1074,127 @@ void set_error(ccsd_handle c, const char* msg) {
 }
 }  // namespace ccsd
 
+namespace {
+// status-returning wrapper for calls without a handle
+template <typename F>
+ccsd_status unguarded(F&& f) {
+  try {
+    f();
+    return CCSD_OK;
+  } catch (const Err& e) {
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    return CCSD_ERR_OOM;
+  } catch (const std::exception& e) {
+    return std::string(e.what()).find("out of memory") != std::string::npos ? CCSD_ERR_OOM : CCSD_ERR_CUDA;
+  }
+}
+
+// device copy of a float array given as host or device memory
+void floats_to_device(const float* src, int64_t n, DevBuf& dst) {
+  dst.alloc((n + 1) / 2);
+  CUDA_OK(cudaMemcpy(dst.p, src, n * sizeof(float), cudaMemcpyDefault));
+}
+}  // namespace
+
 extern "C" {
+
+
+ccsd_status ccsd_mlp_train(const float* X, const float* T, long long n, int steps, int batch, float lr,
+                           unsigned long long seed, float* model_out, float* final_loss) {
+  if (!X || !T || !model_out || n < 1 || steps < 0 || batch < 1) return CCSD_ERR_ARG;
+  return unguarded([&] {
+    // normalisation from the data (host copies)
+    std::vector<float> hx(n * 3), ht(n);
+    CUDA_OK(cudaMemcpy(hx.data(), X, n * 3 * sizeof(float), cudaMemcpyDefault));
+    CUDA_OK(cudaMemcpy(ht.data(), T, n * sizeof(float), cudaMemcpyDefault));
+    std::vector<float> model(mlp::kParams, 0.f);
+    mlp::init_weights(model.data(), seed);
+    for (int d = 0; d < 3; ++d) {
+      double s = 0, s2 = 0;
+      for (long long r = 0; r < n; ++r) {
+        s += hx[r * 3 + d];
+        s2 += (double)hx[r * 3 + d] * hx[r * 3 + d];
+      }
+      double mean = s / n, var = std::max(s2 / n - mean * mean, 1e-30);
+      model[mlp::kTrainable + d] = (float)mean;
+      model[mlp::kTrainable + 3 + d] = (float)std::sqrt(var);
+    }
+    double t2 = 0;
+    for (long long r = 0; r < n; ++r) t2 += (double)ht[r] * ht[r];
+    model[mlp::kTrainable + 6] = (float)std::max(std::sqrt(t2 / n), 1e-30);
+    DevBuf dX, dT, dM, dG((mlp::kTrainable + 1) / 2), dm((mlp::kTrainable + 1) / 2), dv((mlp::kTrainable + 1) / 2),
+        didx(batch), dloss(1);
+    floats_to_device(hx.data(), n * 3, dX);
+    floats_to_device(ht.data(), n, dT);
+    floats_to_device(model.data(), mlp::kParams, dM);
+    CUDA_OK(cudaMemset(dm.p, 0, mlp::kTrainable * sizeof(float)));
+    CUDA_OK(cudaMemset(dv.p, 0, mlp::kTrainable * sizeof(float)));
+    const int b = (int)std::min<long long>(batch, n);
+    for (int s = 0; s < steps; ++s) {
+      const float rate = 0.5f * lr * (1.f + std::cos(3.14159265f * (float)s / (float)std::max(steps, 1)));
+      mlp::sample((int64_t*)didx.p, b, n, seed ^ 0x5bd1e995ull, (unsigned long long)s, 0);
+      mlp::gradient((const float*)dM.p, (const float*)dX.p, (const float*)dT.p, (const int64_t*)didx.p, b,
+                    (float*)dG.p, (float*)dloss.p, 0);
+      mlp::adam((float*)dM.p, (const float*)dG.p, (float*)dm.p, (float*)dv.p, rate, s + 1, 0);
+    }
+    if (final_loss) {
+      mlp::gradient((const float*)dM.p, (const float*)dX.p, (const float*)dT.p, nullptr, n, (float*)dG.p,
+                    (float*)dloss.p, 0);
+      CUDA_OK(cudaMemcpy(final_loss, dloss.p, sizeof(float), cudaMemcpyDeviceToHost));
+    }
+    CUDA_OK(cudaMemcpy(model_out, dM.p, mlp::kParams * sizeof(float), cudaMemcpyDefault));
+    CUDA_OK(cudaDeviceSynchronize());
+  });
+}
+
+ccsd_status ccsd_mlp_predict(const float* model, const float* X, long long n, float* out) {
+  if (!model || !X || !out || n < 1) return CCSD_ERR_ARG;
+  return unguarded([&] {
+    DevBuf dM, dX, dO((n + 1) / 2);
+    floats_to_device(model, mlp::kParams, dM);
+    floats_to_device(X, n * 3, dX);
+    mlp::predict((const float*)dM.p, (const float*)dX.p, n, (float*)dO.p, 0);
+    CUDA_OK(cudaMemcpy(out, dO.p, n * sizeof(float), cudaMemcpyDefault));
+  });
+}
+
+ccsd_status ccsd_mlp_gradient(const float* model, const float* X, const float* T, long long n, float* grad,
+                              float* loss) {
+  if (!model || !X || !T || !grad || n < 1) return CCSD_ERR_ARG;
+  return unguarded([&] {
+    DevBuf dM, dX, dT, dG((mlp::kTrainable + 1) / 2), dL(1);
+    floats_to_device(model, mlp::kParams, dM);
+    floats_to_device(X, n * 3, dX);
+    floats_to_device(T, n, dT);
+    mlp::gradient((const float*)dM.p, (const float*)dX.p, (const float*)dT.p, nullptr, n, (float*)dG.p,
+                  (float*)dL.p, 0);
+    CUDA_OK(cudaMemcpy(grad, dG.p, mlp::kTrainable * sizeof(float), cudaMemcpyDefault));
+    if (loss) CUDA_OK(cudaMemcpy(loss, dL.p, sizeof(float), cudaMemcpyDeviceToHost));
+  });
+}
+
+ccsd_status ccsd_guess_features(ccsd_handle c, float* X) {
+  return guarded(c, [&] {
+    if (!X) throw Err(CCSD_ERR_ARG, "null output");
+    const int64_t n2 = c->dim - c->n1;
+    DevBuf dX((n2 * 3 + 1) / 2);
+    const double* gov = c->ex->ptr(c->P.cp.g.id("Govov"));
+    mlp::features(gov, c->eps.p, c->o, c->v, (float*)dX.p, c->st);
+    CUDA_OK(cudaMemcpyAsync(X, dX.p, n2 * 3 * sizeof(float), cudaMemcpyDefault, c->st));
+    sync(c);
+  });
+}
+
+ccsd_status ccsd_set_guess_model(ccsd_handle c, const float* model) {
+  return guarded(c, [&] {
+    if (!model) {
+      c->guess_model.release();
+      return;
+    }
+    floats_to_device(model, mlp::kParams, c->guess_model);
+  });
+}
 
 ccsd_status ccsd_profile_start(ccsd_handle c) {
   return guarded(c, [&] {

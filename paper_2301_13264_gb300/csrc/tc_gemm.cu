@@ -269,10 +269,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const bool ready = mbar_wait(done, 0, err);
   fence_after();
   if (!ready) atomicExch((int*)p.err, 1);
+  const bool split = (gridDim.z > 1);
+  const bool ostr = !split && p.ostr;
+  // strided output: the tile's column offsets, computed once into the stage
+  // buffers (idle once the done barrier has fired: every MMA and every copy
+  // feeding it has completed)
+  long long* coloff = reinterpret_cast<long long*>(sA);
+  if (ostr && ready)
+    for (int c = threadIdx.x; c < BN; c += NTHREADS) coloff[c] = (n0 + c < p.N) ? dim_offset(n0 + c, p.on) : 0;
+  __syncthreads();
   if (ready && !*err && iters > 0) {
     const int row = m0 + warp * 32 + lane;
-    const bool split = (gridDim.z > 1);
-    const bool ostr = !split && p.ostr;
     double* crow = split ? p.part + ((long long)blockIdx.z * p.M + row) * p.N
                          : (ostr ? p.C + (row < p.M ? dim_offset(row, p.om) : 0) : p.C + (long long)row * p.sCm);
     const long long cs = split ? 1 : p.sCn;
@@ -285,7 +292,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int j = 0; j < 32; ++j) {
           const int n = n0 + c + j;
           if (n < p.N) {
-            double* dst = crow + (ostr ? dim_offset(n, p.on) : (long long)n * cs);
+            double* dst = crow + (ostr ? coloff[c + j] : (long long)n * cs);
             const double v = p.alpha * (double)__uint_as_float(r[j]);
             *dst = (split || p.beta_zero) ? v : (*dst + v);
           }

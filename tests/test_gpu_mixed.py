@@ -81,7 +81,7 @@ def test_mixed_pipeline_energy_and_couplings():
     H = workload("small")
     S_ = System(H.eps, H.h, H.B, H.o)
     res = S_.run(2, tol=1e-12, tol_eom=1e-10, tol_lin=1e-12)
-    h = mixed(H, 3, tol_res=3e-6, tol_eom=1e-5, tol_lin=3e-6, max_iter=200)
+    h = mixed(H, 3, tol_res=3e-6, tol_eom=1e-5, tol_lin=3e-6, max_iter=200, refine=0)
     try:
         e, _ = B.ccsd_solve_ground(h)
         w, _ = B.eom_solve_right(h, 2)
@@ -95,6 +95,31 @@ def test_mixed_pipeline_energy_and_couplings():
     for (k, l), f in F.items():
         ref = S_.coupling(res, k, l, H.h1, H.B1, tol_lin=1e-12)
         assert abs(f - ref) < 1e-3 * abs(ref)
+
+
+@pytest.mark.parametrize("S", [2, 3])
+def test_refined_mixed_pipeline_meets_fp64_tolerances(S):
+    """Tensor-core products everywhere (tc_min_flops = 0) with FP64 refinement of
+    every solve and FP64 densities: the FP64 tolerances of the method hold,
+    energies within 1e-9 Eh, excitation energies within 1e-8, couplings within
+    1e-7 relative of the oracle."""
+    H = workload("small")
+    S_ = System(H.eps, H.h, H.B, H.o)
+    res = S_.run(2, tol=1e-12, tol_eom=1e-10, tol_lin=1e-12)
+    h = mixed(H, S, tol_res=1e-11, tol_eom=1e-9, tol_lin=1e-11, max_iter=200, refine=1)
+    try:
+        e, _ = B.ccsd_solve_ground(h)
+        w, _ = B.eom_solve_right(h, 2)
+        B.eom_solve_left(h, 2)
+        F = {kl: B.ccsd_derivative_coupling(h, kl[0], kl[1], 1, H.h1, H.B1)[0] for kl in [(1, 2), (0, 1), (2, 0)]}
+        assert B.ccsd_stats(h)["tc_gemms"] > 0
+    finally:
+        B.ccsd_destroy(h)
+    assert abs(e - res.e_ccsd) < 1e-9
+    assert np.abs(np.array(w) - np.array(res.omega)).max() < 1e-8
+    for (k, l), f in F.items():
+        ref = S_.coupling(res, k, l, H.h1, H.B1, tol_lin=1e-12)
+        assert abs(f - ref) < 1e-7 * abs(ref)
 
 
 @pytest.mark.parametrize("S", [3])
