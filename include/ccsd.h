@@ -77,6 +77,8 @@ typedef struct {
   int refine;           /* mixed mode: 1 = refine every solve to the FP64 tolerances above (FP64 residuals
                            with mixed-precision correction solves); 0 = stop at the mixed-precision floor */
   double tol_switch;    /* mixed mode with refine: residual level at which the FP64 refinement starts */
+  int autotune;         /* mixed mode: 1 = time the tensor-core tile widths and split counts once per GEMM
+                           shape and keep the fastest; 0 = choose them from the output width */
 } ccsd_options;
 
 /* Fill *opt with defaults (FP64, tol_res 1e-10, tol_eom 1e-7, tol_lin 1e-9, ...). */
@@ -167,6 +169,39 @@ ccsd_status ccsd_guess_features(ccsd_handle h, float* X);
 /* Use `model` for the starting doubles of the next ccsd_solve_ground (NULL: the
  * MP2-type start).  The model is copied. */
 ccsd_status ccsd_set_guess_model(ccsd_handle h, const float* model);
+
+/* ---- batches of systems -----------------------------------------------------
+ * Many small systems underuse the GPU one at a time.  A batch groups handles
+ * (systems of any o, v, naux) so that the block Jacobian transforms of all of
+ * them run as one CUDA graph launch: the transforms of nvec vectors per system
+ * are captured once per side (and per set of active systems) and replayed on
+ * every later call; inside the graph each system's kernels run on a stream of
+ * its own, so the systems' kernels overlap.  The first call for a side runs the
+ * transforms without a graph (this also fixes every lazily built cache and, with
+ * opt.autotune, the tile choices) and then captures the graph.
+ * While a handle belongs to a batch its calls run on a stream the batch created;
+ * ccsd_batch_destroy restores the handle's own stream.  The handles must outlive
+ * the batch, and no handle of a batch may be used concurrently with a batch call.
+ * (An extension of the method's solvers: the paper treats one system at a time.) */
+typedef struct ccsd_batch_ctx* ccsd_batch;
+/* nsys >= 1 distinct handles; nvec (1..16) trial vectors per system and launch. */
+ccsd_status ccsd_batch_create(int nsys, const ccsd_handle* systems, int nvec, ccsd_batch* out);
+/* y[s] = A x[s] (side 0) or (x[s]^T A)^T (side 1) for the nvec vectors of system s;
+ * x[s], y[s] are [nvec][dim_s] arrays in host or device memory.  Every system needs
+ * amplitudes (ccsd_solve_ground or ccsd_set_amplitudes). */
+ccsd_status ccsd_batch_transform(ccsd_batch b, int side, const double* const* x, double* const* y);
+/* Lockstep block Davidson over all systems for the nroots (<= nvec) lowest roots:
+ * per iteration the new trial vectors of every unconverged system are transformed
+ * by one graph launch (each system's block padded with zero vectors to nvec).
+ * side 0 leaves every handle as eom_solve_right does, side 1 as eom_solve_left
+ * (side 0 first).  Under FP64 refinement (mixed precision with opt.refine) the
+ * batched phase stops at 10 tol_switch and each system finishes with its own FP64
+ * continuation.  omega[nsys*nroots], iters[nsys] (either may be NULL). */
+ccsd_status ccsd_batch_eom_solve(ccsd_batch b, int side, int nroots, double* omega, int* iters);
+/* Graph launches, graph captures and kernel nodes of the last captured graph. */
+ccsd_status ccsd_batch_stats(ccsd_batch b, long long* launches, long long* captures, long long* nodes);
+const char* ccsd_batch_last_error(ccsd_batch b);
+void ccsd_batch_destroy(ccsd_batch b);
 
 /* Allocation-free variant of ccsd_derivative_coupling (the paper has no
  * counterpart; this is a service for callers that cannot allocate device

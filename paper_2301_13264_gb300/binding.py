@@ -38,6 +38,7 @@ class Options(ctypes.Structure):
         ("tc_min_flops", ctypes.c_double),
         ("refine", ctypes.c_int),
         ("tol_switch", ctypes.c_double),
+        ("autotune", ctypes.c_int),
     ]
 
 
@@ -322,3 +323,58 @@ def ccsd_guess_features(h, X):
 def ccsd_set_guess_model(h, model):
     f = _mlp_fn("ccsd_set_guess_model", [_P, _P])
     _check(h, f(h, None if model is None else _fptr(model, MLP_PARAMS)))
+
+
+# ---- batches of systems -----------------------------------------------------
+
+def _batch_fn(name, argtypes, restype=ctypes.c_int):
+    f = getattr(lib(), name)
+    if not getattr(f, "argtypes", None):
+        f.argtypes = argtypes
+        f.restype = restype
+    return f
+
+
+def _bcheck(b, status):
+    if status != OK:
+        f = _batch_fn("ccsd_batch_last_error", [_P], ctypes.c_char_p)
+        msg = f(b).decode() if b else lib().ccsd_strerror(status).decode()
+        raise CCSDError(status, msg)
+
+
+def ccsd_batch_create(handles, nvec=8):
+    arr = (_P * len(handles))(*[h.value if isinstance(h, _P) else h for h in handles])
+    out = _P()
+    f = _batch_fn("ccsd_batch_create", [ctypes.c_int, ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P)])
+    _bcheck(None, f(len(handles), arr, nvec, ctypes.byref(out)))
+    return out
+
+
+def ccsd_batch_transform(b, side, xs, ys):
+    """ys[s] = transform of xs[s] ([nvec][dim_s] float64 arrays, host or device) for every system."""
+    n = len(xs)
+    xa = (_P * n)(*[_ptr(x).value for x in xs])
+    ya = (_P * n)(*[_ptr(y).value for y in ys])
+    f = _batch_fn("ccsd_batch_transform", [_P, ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P)])
+    _bcheck(b, f(b, side, xa, ya))
+
+
+def ccsd_batch_eom_solve(b, side, nroots, nsys):
+    w = np.zeros(nsys * nroots)
+    it = (ctypes.c_int * nsys)()
+    f = _batch_fn("ccsd_batch_eom_solve", [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_int)])
+    _bcheck(b, f(b, side, nroots, _ptr(w), it))
+    return w.reshape(nsys, nroots), list(it)
+
+
+def ccsd_batch_stats(b):
+    la, ca, na = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+    f = _batch_fn("ccsd_batch_stats", [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                       ctypes.POINTER(ctypes.c_longlong)])
+    _bcheck(b, f(b, ctypes.byref(la), ctypes.byref(ca), ctypes.byref(na)))
+    return {"launches": la.value, "captures": ca.value, "nodes": na.value}
+
+
+def ccsd_batch_destroy(b):
+    if b:
+        _batch_fn("ccsd_batch_destroy", [_P], None)(b)

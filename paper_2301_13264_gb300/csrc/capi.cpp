@@ -174,6 +174,23 @@ void right_block(ccsd_ctx* c, const double* X, double* Y, int nvec) {
 }
 
 // Y = (X^T A)^T for nvec vectors; with eseed != 0 adds eseed * eta (used for eta itself)
+// the left transform with caller-provided work arrays W, G ([nvec][dim] each) and
+// a zero energy seed: no allocation, no host copy, no synchronisation
+void left_block_into(ccsd_ctx* c, const double* X, double* Y, int nvec, double* W, double* G) {
+  Executor& ex = *c->ex;
+  auto& P = c->P;
+  ex.set_nvec(nvec);
+  launch_weight(c->vs, X, W, nvec, c->dim, c->st);
+  CUDA_OK(cudaMemsetAsync(c->seedE.p, 0, nvec * sizeof(double), c->st));
+  ex.bind(P.zL1, W, c->dim);
+  ex.bind(P.zL2, W + c->n1, c->dim);
+  ex.bind(P.zLE, c->seedE.p);
+  ex.bind(P.zLA1, G, c->dim);
+  ex.bind(P.zLA2, G + c->n1, c->dim);
+  ex.run(P.vjp_z);
+  launch_packed_grad(c->vs, G, Y, nvec, c->dim, c->st);
+}
+
 void left_block(ccsd_ctx* c, const double* X, double* Y, int nvec, double eseed = 0.0) {
   ensure_cache(c);
   Executor& ex = *c->ex;
@@ -334,94 +351,102 @@ int solve_left_linear(ccsd_ctx* c, const double* rhs, double* x, double tol) {
 }
 
 // ---------------------------------------------------------------------------
-// Davidson for the lowest nroots of A (side 0) or A^T (side 1)
+// Davidson for the lowest nroots of A (side 0) or A^T (side 1), as a state
+// machine: the caller transforms the pending trial vectors V[first, first+count)
+// into AV[first, first+count) (one system at a time, or many systems in one
+// batched launch) and then calls advance(), which extends the projected matrix,
+// solves the subspace problem and either converges or queues new trial vectors.
 // ---------------------------------------------------------------------------
-int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std::vector<std::unique_ptr<DevBuf>>& out,
-             double tol, const std::vector<std::unique_ptr<DevBuf>>* init = nullptr) {
-  const int64_t dim = c->dim;
-  const int maxsub = std::max(c->opt.davidson_max_sub, 3 * nroots);
-  const int block = std::max(1, std::min(c->opt.davidson_block, 16));
-  DevBuf V(maxsub * dim), AV(maxsub * dim);
-  int m = 0;
-  std::vector<double> Gm(maxsub * maxsub, 0.0);  // Gm[i][j] = <V_i | A V_j>
-  auto apply = [&](int first, int count) {
-    for (int s = 0; s < count; s += block) {
-      int nb = std::min(block, count - s);
-      double* X = V.p + (first + s) * dim;
-      double* Y = AV.p + (first + s) * dim;
-      if (side == 0)
-        right_block(c, X, Y, nb);
-      else
-        left_block(c, X, Y, nb);
-    }
-    // extend the projected matrix
-    std::vector<double> a = gram(c, V.p, dim, first + count, AV.p + first * dim, dim, count);
-    std::vector<double> b = gram(c, V.p + first * dim, dim, count, AV.p, dim, first);
-    for (int i = 0; i < first + count; ++i)
-      for (int j = 0; j < count; ++j) Gm[i * maxsub + first + j] = a[i * count + j];
-    for (int i = 0; i < count; ++i)
-      for (int j = 0; j < first; ++j) Gm[(first + i) * maxsub + j] = b[i * first + j];
-  };
-  // orthonormalise candidate vectors in place (slots m..m+cnt-1); returns number kept
-  auto orthonormalize = [&](int cnt) {
-    int kept = 0;
-    for (int q = 0; q < cnt; ++q) {
-      double* x = V.p + (m + q) * dim;
-      std::vector<double> nrm0 = gram(c, x, dim, 1, x, dim, 1);
-      if (!(nrm0[0] > 0.0)) continue;
-      launch_axpby(dim, 1.0 / std::sqrt(nrm0[0]), x, 0.0, x, c->st);
-      int have = m + kept;
-      for (int pass = 0; pass < 2; ++pass) {
-        if (have == 0) break;
-        std::vector<double> d = gram(c, V.p, dim, have, x, dim, 1);
-        std::vector<double> coef(have);
-        for (int i = 0; i < have; ++i) coef[i] = -d[i];
-        lincomb(c, V.p, dim, have, coef, x, dim, 1, true);
-      }
-      std::vector<double> nrm = gram(c, x, dim, 1, x, dim, 1);
-      if (nrm[0] < 1e-16) continue;
-      double* dst = V.p + (m + kept) * dim;
-      launch_axpby(dim, 1.0 / std::sqrt(nrm[0]), x, 0.0, dst, c->st);
-      ++kept;
-    }
-    return kept;
-  };
-  // guesses: the given vectors, else singles unit vectors of the lowest orbital-energy differences
-  if (init && (int)init->size() >= nroots) {
-    for (int g = 0; g < nroots; ++g)
-      CUDA_OK(cudaMemcpyAsync(V.p + g * dim, (*init)[g]->p, dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-    int kept = orthonormalize(nroots);
-    apply(0, kept);
-    m = kept;
-  } else {
-    std::vector<double> eps(c->n);
-    CUDA_OK(cudaMemcpy(eps.data(), c->eps.p, c->n * sizeof(double), cudaMemcpyDeviceToHost));
-    std::vector<std::pair<double, int>> d1;
-    for (int i = 0; i < c->o; ++i)
-      for (int a = 0; a < c->v; ++a) d1.push_back({eps[c->o + a] - eps[i], i * c->v + a});
-    std::stable_sort(d1.begin(), d1.end(), [](auto& x, auto& y) { return x.first < y.first; });
-    int ng = std::min<int>(nroots, (int)d1.size());
-    CUDA_OK(cudaMemsetAsync(V.p, 0, ng * dim * sizeof(double), c->st));
-    for (int g = 0; g < ng; ++g) {
-      double one = 1.0;
-      CUDA_OK(cudaMemcpyAsync(V.p + g * dim + d1[g].second, &one, sizeof(double), cudaMemcpyHostToDevice, c->st));
+class Davidson {
+ public:
+  Davidson(ccsd_ctx* c, int side, int nroots, double tol, const std::vector<std::unique_ptr<DevBuf>>* init)
+      : c_(c),
+        side(side),
+        nroots_(nroots),
+        tol_(tol),
+        dim_(c->dim),
+        maxsub_(std::max(c->opt.davidson_max_sub, 3 * nroots)),
+        V(maxsub_ * c->dim),
+        AV(maxsub_ * c->dim),
+        X(nroots * c->dim),
+        AX(nroots * c->dim),
+        Rz(nroots * c->dim),
+        Gm(maxsub_ * maxsub_, 0.0) {
+    const int64_t dim = dim_;
+    // guesses: the given vectors, else singles unit vectors of the lowest orbital-energy differences
+    if (init && (int)init->size() >= nroots) {
+      for (int g = 0; g < nroots; ++g)
+        CUDA_OK(cudaMemcpyAsync(V.p + g * dim, (*init)[g]->p, dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+      count = orthonormalize(nroots);
+    } else {
+      std::vector<double> eps(c->n);
+      CUDA_OK(cudaMemcpyAsync(eps.data(), c->eps.p, c->n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
       sync(c);
+      std::vector<std::pair<double, int>> d1;
+      for (int i = 0; i < c->o; ++i)
+        for (int a = 0; a < c->v; ++a) d1.push_back({eps[c->o + a] - eps[i], i * c->v + a});
+      std::stable_sort(d1.begin(), d1.end(), [](auto& x, auto& y) { return x.first < y.first; });
+      // a few more start vectors than roots, so that a low root is not missed
+      int ng = std::min<int>(nroots + std::min(nroots, 4), (int)d1.size());
+      CUDA_OK(cudaMemsetAsync(V.p, 0, ng * dim * sizeof(double), c->st));
+      std::vector<double> one(ng, 1.0);
+      for (int g = 0; g < ng; ++g)
+        CUDA_OK(cudaMemcpyAsync(V.p + g * dim + d1[g].second, &one[g], sizeof(double), cudaMemcpyHostToDevice,
+                                c->st));
+      sync(c);
+      count = orthonormalize(ng);
     }
-    int kept = orthonormalize(ng);
-    apply(0, kept);
-    m = kept;
+    if (count == 0) throw Err(CCSD_ERR_NOT_CONVERGED, "no Davidson start vectors");
   }
-  DevBuf X(nroots * dim), AX(nroots * dim), Rz(nroots * dim);
-  int complex_run = 0;
-  for (int it = 1; it <= c->opt.max_iter; ++it) {
+
+  // pending trial vectors and their transforms
+  int first = 0, count = 0;
+  double* vin(int q) { return V.p + (first + q) * dim_; }
+  double* vout(int q) { return AV.p + (first + q) * dim_; }
+  int iterations = 0;
+  std::vector<double> omega;
+  const int side;
+  // when set (nroots values), follow the Ritz values nearest these instead of the lowest
+  std::vector<double> targets;
+
+  // transforms of the pending vectors are in place: returns true once converged
+  bool advance() {
+    ccsd_ctx* c = c_;
+    const int64_t dim = dim_;
+    ++iterations;
+    // extend the projected matrix with the pending block
+    {
+      std::vector<double> a = gram(c, V.p, dim, first + count, AV.p + first * dim, dim, count);
+      std::vector<double> b = gram(c, V.p + first * dim, dim, count, AV.p, dim, first);
+      for (int i = 0; i < first + count; ++i)
+        for (int j = 0; j < count; ++j) Gm[i * maxsub_ + first + j] = a[i * count + j];
+      for (int i = 0; i < count; ++i)
+        for (int j = 0; j < first; ++j) Gm[(first + i) * maxsub_ + j] = b[i * first + j];
+    }
+    m_ = first + count;
+    count = 0;
+    const int m = m_, nroots = nroots_;
     std::vector<double> G(m * m);
     for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) G[i * m + j] = Gm[i * maxsub + j];
-    std::vector<std::complex<double>> ev = eigenvalues(m, G);
-    std::sort(ev.begin(), ev.end(), [](auto& a, auto& b) { return a.real() < b.real(); });
-    if ((int)ev.size() < nroots) throw Err(CCSD_ERR_NOT_CONVERGED, "subspace too small");
+      for (int j = 0; j < m; ++j) G[i * m + j] = Gm[i * maxsub_ + j];
+    std::vector<std::complex<double>> all = eigenvalues(m, G);
+    std::sort(all.begin(), all.end(), [](auto& a, auto& b) { return a.real() < b.real(); });
+    if ((int)all.size() < nroots) throw Err(CCSD_ERR_NOT_CONVERGED, "subspace too small");
     double scale = 0.0;
-    for (auto& e : ev) scale = std::max(scale, std::abs(e));
+    for (auto& e : all) scale = std::max(scale, std::abs(e));
+    // wanted roots: the lowest by real part, or the ones nearest the given targets
+    std::vector<std::complex<double>> ev(all.begin(), all.begin() + nroots);
+    if ((int)targets.size() == nroots) {
+      std::vector<char> used(all.size(), 0);
+      for (int k = 0; k < nroots; ++k) {
+        int best = -1;
+        for (int q = 0; q < (int)all.size(); ++q)
+          if (!used[q] && (best < 0 || std::fabs(all[q].real() - targets[k]) < std::fabs(all[best].real() - targets[k])))
+            best = q;
+        used[best] = 1;
+        ev[k] = all[best];
+      }
+    }
     // A complex pair a +- ib among the wanted subspace eigenvalues is usually
     // transient (a small subspace of a non-symmetric matrix); the pair's real 2-D
     // invariant subspace is then spanned by u (inverse iteration at a) and (G - a)u,
@@ -429,8 +454,8 @@ int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std:
     // many expansions is reported.
     bool cplx = false;
     for (int k = 0; k < nroots; ++k) cplx |= std::fabs(ev[k].imag()) > 1e-9 * std::max(scale, 1.0);
-    complex_run = cplx ? complex_run + 1 : 0;
-    if (complex_run > 12) throw Err(CCSD_ERR_COMPLEX_ROOT, "complex eigenvalue among the wanted roots");
+    complex_run_ = cplx ? complex_run_ + 1 : 0;
+    if (complex_run_ > 12) throw Err(CCSD_ERR_COMPLEX_ROOT, "complex eigenvalue among the wanted roots");
     std::vector<double> U(m * nroots);
     omega.assign(nroots, 0.0);
     std::vector<double> prev;
@@ -473,46 +498,117 @@ int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std:
     }
     std::vector<double> rn = gram(c, Rz.p, dim, nroots, Rz.p, dim, nroots);
     for (int k = 0; k < nroots; ++k)
-      if (std::sqrt(std::max(rn[k * nroots + k], 0.0)) > tol) todo.push_back(k);
-    if (todo.empty() && !cplx) {
-      out.clear();
-      for (int k = 0; k < nroots; ++k) {
-        out.emplace_back(new DevBuf(dim));
-        CUDA_OK(cudaMemcpyAsync(out[k]->p, X.p + k * dim, dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-      }
-      sync(c);
-      return it;
-    }
-    if (m + (int)todo.size() > maxsub) {  // restart from the current Ritz vectors
+      if (std::sqrt(std::max(rn[k * nroots + k], 0.0)) > tol_) todo.push_back(k);
+    if (todo.empty() && !cplx) return true;
+    if (iterations >= c->opt.max_iter) throw Err(CCSD_ERR_NOT_CONVERGED, "Davidson not converged");
+    int base = m_;
+    if (m_ + (int)todo.size() > maxsub_) {  // restart from the current Ritz vectors
       CUDA_OK(cudaMemcpyAsync(V.p, X.p, nroots * dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-      m = 0;
-      int kept = orthonormalize(nroots);
       std::fill(Gm.begin(), Gm.end(), 0.0);
-      apply(0, kept);
-      m = kept;
+      base = 0;
+      m_ = 0;
+      for (size_t q = 0; q < todo.size(); ++q)
+        launch_precond(c->vs, c->eps.p, Rz.p + todo[q] * dim, V.p + (nroots + q) * dim, omega[todo[q]], c->st);
+      first = 0;
+      count = orthonormalize(nroots + (int)todo.size());
+    } else {
+      for (size_t q = 0; q < todo.size(); ++q)
+        launch_precond(c->vs, c->eps.p, Rz.p + todo[q] * dim, V.p + (base + q) * dim, omega[todo[q]], c->st);
+      first = base;
+      count = orthonormalize((int)todo.size());
     }
-    for (size_t q = 0; q < todo.size(); ++q) {
-      int k = todo[q];
-      launch_precond(c->vs, c->eps.p, Rz.p + k * dim, V.p + (m + q) * dim, omega[k], c->st);
-    }
-    int kept = orthonormalize((int)todo.size());
-    if (kept == 0) throw Err(CCSD_ERR_NOT_CONVERGED, "Davidson stagnated");
-    apply(m, kept);
-    m += kept;
+    if (count == 0) throw Err(CCSD_ERR_NOT_CONVERGED, "Davidson stagnated");
+    return false;
   }
-  throw Err(CCSD_ERR_NOT_CONVERGED, "Davidson not converged");
+
+  // the converged Ritz vectors (after advance() returned true)
+  void results(std::vector<std::unique_ptr<DevBuf>>& out) {
+    out.clear();
+    for (int k = 0; k < nroots_; ++k) {
+      out.emplace_back(new DevBuf(dim_));
+      CUDA_OK(cudaMemcpyAsync(out[k]->p, X.p + k * dim_, dim_ * sizeof(double), cudaMemcpyDeviceToDevice, c_->st));
+    }
+    sync(c_);
+  }
+
+ private:
+  // orthonormalise candidates in slots m_..m_+cnt-1 against V[0, m_) and each
+  // other, compacting the kept ones to the front; returns the number kept
+  int orthonormalize(int cnt) {
+    ccsd_ctx* c = c_;
+    const int64_t dim = dim_;
+    int kept = 0;
+    for (int q = 0; q < cnt; ++q) {
+      double* x = V.p + (m_ + q) * dim;
+      std::vector<double> nrm0 = gram(c, x, dim, 1, x, dim, 1);
+      if (!(nrm0[0] > 0.0)) continue;
+      launch_axpby(dim, 1.0 / std::sqrt(nrm0[0]), x, 0.0, x, c->st);
+      int have = m_ + kept;
+      for (int pass = 0; pass < 2; ++pass) {
+        if (have == 0) break;
+        std::vector<double> d = gram(c, V.p, dim, have, x, dim, 1);
+        std::vector<double> coef(have);
+        for (int i = 0; i < have; ++i) coef[i] = -d[i];
+        lincomb(c, V.p, dim, have, coef, x, dim, 1, true);
+      }
+      std::vector<double> nrm = gram(c, x, dim, 1, x, dim, 1);
+      if (nrm[0] < 1e-16) continue;
+      double* dst = V.p + (m_ + kept) * dim;
+      launch_axpby(dim, 1.0 / std::sqrt(nrm[0]), x, 0.0, dst, c->st);
+      ++kept;
+    }
+    return kept;
+  }
+
+  ccsd_ctx* c_;
+  int nroots_;
+  double tol_;
+  int64_t dim_;
+  int maxsub_;
+  DevBuf V, AV, X, AX, Rz;
+  std::vector<double> Gm;  // Gm[i][j] = <V_i | A V_j>
+  int m_ = 0;
+  int complex_run_ = 0;
+};
+
+// transforms of the pending Davidson vectors on the system's own stream
+void transform_pending(Davidson& d, ccsd_ctx* c) {
+  const int block = std::max(1, std::min(c->opt.davidson_block, 16));
+  for (int s = 0; s < d.count; s += block) {
+    const int nb = std::min(block, d.count - s);
+    if (d.side == 0)
+      right_block(c, d.vin(s), d.vout(s), nb);
+    else
+      left_block(c, d.vin(s), d.vout(s), nb);
+  }
+}
+
+int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std::vector<std::unique_ptr<DevBuf>>& out,
+             double tol, const std::vector<std::unique_ptr<DevBuf>>* init = nullptr,
+             const std::vector<double>* targets = nullptr) {
+  Davidson d(c, side, nroots, tol, init);
+  if (targets) d.targets = *targets;
+  for (;;) {
+    transform_pending(d, c);
+    if (d.advance()) break;
+  }
+  omega = d.omega;
+  d.results(out);
+  return d.iterations;
 }
 
 // Davidson to tol_eom; in mixed mode with refinement the mixed-precision solution
-// (to 10 tol_switch) seeds an FP64 continuation, which needs only a few transforms.
+// (to 10 tol_switch) seeds an FP64 continuation that follows the same roots.
 int davidson_refined(ccsd_ctx* c, int side, int nroots, std::vector<double>& w,
                      std::vector<std::unique_ptr<DevBuf>>& out,
-                     const std::vector<std::unique_ptr<DevBuf>>* init = nullptr) {
-  if (!refining(c)) return davidson(c, side, nroots, w, out, c->opt.tol_eom, init);
+                     const std::vector<std::unique_ptr<DevBuf>>* init = nullptr,
+                     const std::vector<double>* targets = nullptr) {
+  if (!refining(c)) return davidson(c, side, nroots, w, out, c->opt.tol_eom, init, targets);
   std::vector<std::unique_ptr<DevBuf>> mixed;
-  int it = davidson(c, side, nroots, w, mixed, std::max(c->opt.tol_eom, 10.0 * c->opt.tol_switch), init);
+  int it = davidson(c, side, nroots, w, mixed, std::max(c->opt.tol_eom, 10.0 * c->opt.tol_switch), init, targets);
   PrecScope fp64(c, CCSD_PREC_FP64);
-  it += davidson(c, side, nroots, w, out, c->opt.tol_eom, &mixed);
+  const std::vector<double> wm = w;
+  it += davidson(c, side, nroots, w, out, c->opt.tol_eom, &mixed, &wm);
   return it;
 }
 
@@ -526,6 +622,45 @@ void normalize_right(ccsd_ctx* c, double* R) {
   CUDA_OK(cudaMemcpyAsync(h2, o2.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   sync(c);
   if (h2[1] < 0) launch_axpby(c->dim, -1.0, R, 0.0, R, c->st);
+}
+
+// right states in c->R with excitation energies w: normalisation, R0 = eta.R / omega
+void finish_right(ccsd_ctx* c, const std::vector<double>& w) {
+  const int nroots = (int)w.size();
+  c->omega = w;
+  c->r0.assign(nroots, 0.0);
+  for (int k = 0; k < nroots; ++k) {
+    normalize_right(c, c->R[k]->p);
+    std::vector<double> d = gram(c, c->eta.p, c->dim, 1, c->R[k]->p, c->dim, 1);
+    c->r0[k] = d[0] / w[k];
+  }
+  c->have_right = true;
+  c->have_left = false;
+  c->dens_k = c->dens_l = -1;
+}
+
+// left eigenvectors Lr with excitation energies w: root check against the right
+// solve, then biorthonormalisation L_k = sum_m Minv^T[k][m] Lr_m with M[m][l] = <Lr_m|R_l>
+void finish_left(ccsd_ctx* c, const std::vector<double>& w, const std::vector<std::unique_ptr<DevBuf>>& Lr) {
+  const int nroots = (int)w.size();
+  for (int k = 0; k < nroots; ++k)
+    if (std::fabs(w[k] - c->omega[k]) > 1e-5 * std::max(1.0, std::fabs(c->omega[k])))
+      throw Err(CCSD_ERR_NOT_CONVERGED, "left and right roots differ: root " + std::to_string(k) + " left " +
+                                            std::to_string(w[k]) + " right " + std::to_string(c->omega[k]));
+  std::vector<double> M(nroots * nroots);
+  for (int k = 0; k < nroots; ++k)
+    for (int l = 0; l < nroots; ++l) M[k * nroots + l] = gram(c, Lr[k]->p, c->dim, 1, c->R[l]->p, c->dim, 1)[0];
+  std::vector<double> Minv;
+  if (!invert(nroots, M, Minv)) throw Err(CCSD_ERR_DEGENERATE, "left/right overlap matrix is singular");
+  c->L.clear();
+  for (int k = 0; k < nroots; ++k) {
+    c->L.emplace_back(new DevBuf(c->dim));
+    CUDA_OK(cudaMemsetAsync(c->L[k]->p, 0, c->dim * sizeof(double), c->st));
+    for (int m = 0; m < nroots; ++m) launch_axpby(c->dim, Minv[k * nroots + m], Lr[m]->p, 1.0, c->L[k]->p, c->st);
+  }
+  sync(c);
+  c->have_left = true;
+  c->dens_k = c->dens_l = -1;
 }
 
 ccsd_status fail(ccsd_ctx* c, ccsd_status s, const std::string& msg) {
@@ -655,6 +790,7 @@ void ccsd_default_options(ccsd_options* opt) {
   opt->tc_min_flops = 2.0e9;
   opt->refine = 1;
   opt->tol_switch = 1e-6;
+  opt->autotune = 0;
 }
 
 const char* ccsd_strerror(ccsd_status s) {
@@ -739,6 +875,7 @@ ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int
     Executor& ex = *c->ex;
     ex.set_precision(c->opt.precision, c->opt.splits);
     ex.tc_min_flops = c->opt.tc_min_flops;
+    ex.autotune = c->opt.autotune;
     ex.bind(cp.h, c->h.p);
     ex.bind(cp.B, c->B.p);
     ex.bind(cp.ones_o, c->ones.p);
@@ -876,16 +1013,7 @@ ccsd_status eom_solve_right(ccsd_handle c, int nroots, double* omega, int* iters
     if (!c->have_ground) throw Err(CCSD_ERR_STATE, "ground state not solved");
     std::vector<double> w;
     int it = davidson_refined(c, 0, nroots, w, c->R);
-    c->omega = w;
-    c->r0.assign(nroots, 0.0);
-    for (int k = 0; k < nroots; ++k) {
-      normalize_right(c, c->R[k]->p);
-      std::vector<double> d = gram(c, c->eta.p, c->dim, 1, c->R[k]->p, c->dim, 1);
-      c->r0[k] = d[0] / w[k];
-    }
-    c->have_right = true;
-    c->have_left = false;
-    c->dens_k = c->dens_l = -1;
+    finish_right(c, w);
     if (omega) std::copy(w.begin(), w.end(), omega);
     if (iters) *iters = it;
   });
@@ -898,26 +1026,8 @@ ccsd_status eom_solve_left(ccsd_handle c, int nroots, double* omega, int* iters)
     std::vector<double> w;
     std::vector<std::unique_ptr<DevBuf>> Lr;
     // the right eigenvectors start the left solve: same roots, close vectors
-    int it = davidson_refined(c, 1, nroots, w, Lr, &c->R);
-    for (int k = 0; k < nroots; ++k)
-      if (std::fabs(w[k] - c->omega[k]) > 1e-5 * std::max(1.0, std::fabs(c->omega[k])))
-        throw Err(CCSD_ERR_NOT_CONVERGED, "left and right roots differ");
-    // biorthonormalise: L_new_k = sum_m Minv^T[k][m] L_m with M[m][l] = <L_m|R_l>
-    std::vector<double> M(nroots * nroots);
-    for (int k = 0; k < nroots; ++k)
-      for (int l = 0; l < nroots; ++l) M[k * nroots + l] = gram(c, Lr[k]->p, c->dim, 1, c->R[l]->p, c->dim, 1)[0];
-    std::vector<double> Minv;
-    if (!invert(nroots, M, Minv)) throw Err(CCSD_ERR_DEGENERATE, "left/right overlap matrix is singular");
-    c->L.clear();
-    for (int k = 0; k < nroots; ++k) {
-      c->L.emplace_back(new DevBuf(c->dim));
-      CUDA_OK(cudaMemsetAsync(c->L[k]->p, 0, c->dim * sizeof(double), c->st));
-      for (int m = 0; m < nroots; ++m)
-        launch_axpby(c->dim, Minv[k * nroots + m], Lr[m]->p, 1.0, c->L[k]->p, c->st);
-    }
-    sync(c);
-    c->have_left = true;
-    c->dens_k = c->dens_l = -1;
+    int it = davidson_refined(c, 1, nroots, w, Lr, &c->R, &c->omega);
+    finish_left(c, w, Lr);
     if (omega) std::copy(w.begin(), w.end(), omega);
     if (iters) *iters = it;
   });
@@ -1252,6 +1362,330 @@ long long ccsd_describe_program(const char* which, char* buf, size_t len) {
   } catch (...) {
     return -1;
   }
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// batches of systems: block transforms of all systems as one CUDA graph launch
+// ---------------------------------------------------------------------------
+struct ccsd_batch_ctx {
+  std::vector<ccsd_ctx*> sys;
+  std::vector<cudaStream_t> orig, own;  // each handle's stream before the batch, and the batch's streams
+  cudaStream_t cap = nullptr;           // capture / launch stream
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  int nvec = 8;
+  std::vector<std::unique_ptr<DevBuf>> X, Y, W, G;  // per system [nvec][dim] staging
+  struct Graph {
+    int side;
+    std::vector<char> mask;
+    cudaGraphExec_t exec;
+    long long nodes;
+  };
+  std::vector<Graph> graphs;
+  long long launches = 0, captures = 0, last_nodes = 0;
+  std::string err;
+};
+
+namespace {
+
+template <typename F>
+ccsd_status batch_guarded(ccsd_batch_ctx* b, F&& f) {
+  if (!b) return CCSD_ERR_ARG;
+  try {
+    f();
+    return CCSD_OK;
+  } catch (const Err& e) {
+    b->err = e.what();
+    return e.code;
+  } catch (const DeviceTimeout& e) {
+    b->err = e.what();
+    return CCSD_ERR_TIMEOUT;
+  } catch (const std::bad_alloc&) {
+    b->err = "host allocation failed";
+    return CCSD_ERR_OOM;
+  } catch (const std::exception& e) {
+    b->err = e.what();
+    return b->err.find("out of memory") != std::string::npos ? CCSD_ERR_OOM : CCSD_ERR_CUDA;
+  }
+}
+
+// system s's block transform of its staging vectors, on its own stream, without synchronising
+void batch_block(ccsd_batch_ctx* b, int s, int side) {
+  ccsd_ctx* c = b->sys[s];
+  if (side == 0) {
+    Executor& ex = *c->ex;
+    auto& P = c->P;
+    ex.set_nvec(b->nvec);
+    ex.bind(P.zR1, b->X[s]->p, c->dim);
+    ex.bind(P.zR2, b->X[s]->p + c->n1, c->dim);
+    ex.bind(P.zAR1, b->Y[s]->p, c->dim);
+    ex.bind(P.zAR2, b->Y[s]->p + c->n1, c->dim);
+    ex.bind(P.zAE, c->gsc.p);
+    ex.run(P.jvp_z);
+  } else {
+    left_block_into(c, b->X[s]->p, b->Y[s]->p, b->nvec, b->W[s]->p, b->G[s]->p);
+  }
+}
+
+// Y_s = transform of X_s for the systems in mask: one graph launch once captured
+void batch_run(ccsd_batch_ctx* b, int side, const std::vector<char>& mask) {
+  const int ns = (int)b->sys.size();
+  for (int s = 0; s < ns; ++s)
+    if (mask[s]) {
+      ensure_cache(b->sys[s]);
+      if (side == 1 && !b->W[s]) {
+        b->W[s].reset(new DevBuf(b->nvec * b->sys[s]->dim));
+        b->G[s].reset(new DevBuf(b->nvec * b->sys[s]->dim));
+      }
+    }
+  for (auto& g : b->graphs)
+    if (g.side == side && g.mask == mask) {
+      CUDA_OK(cudaGraphLaunch(g.exec, b->cap));
+      CUDA_OK(cudaStreamSynchronize(b->cap));
+      ++b->launches;
+      count_launches(g.nodes);
+      for (int s = 0; s < ns; ++s)
+        if (mask[s] && b->sys[s]->ex->tc_error() != 0)
+          throw DeviceTimeout("a tensor-core kernel wait exceeded its budget");
+      return;
+    }
+  // first use of this (side, mask): run directly (the result is this call's), then capture
+  for (int s = 0; s < ns; ++s)
+    if (mask[s]) batch_block(b, s, side);
+  for (int s = 0; s < ns; ++s)
+    if (mask[s]) {
+      CUDA_OK(cudaStreamSynchronize(b->sys[s]->st));
+      if (b->sys[s]->ex->tc_error() != 0) throw DeviceTimeout("a tensor-core kernel wait exceeded its budget");
+    }
+  cudaGraph_t graph = nullptr;
+  CUDA_OK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+  try {
+    CUDA_OK(cudaEventRecord(b->fork, b->cap));
+    for (int s = 0; s < ns; ++s) {
+      if (!mask[s]) continue;
+      ccsd_ctx* c = b->sys[s];
+      CUDA_OK(cudaStreamWaitEvent(c->st, b->fork, 0));
+      c->ex->capturing = true;
+      batch_block(b, s, side);
+      c->ex->capturing = false;
+      CUDA_OK(cudaEventRecord(b->join[s], c->st));
+      CUDA_OK(cudaStreamWaitEvent(b->cap, b->join[s], 0));
+    }
+    CUDA_OK(cudaStreamEndCapture(b->cap, &graph));
+  } catch (...) {
+    for (ccsd_ctx* c : b->sys) c->ex->capturing = false;
+    cudaGraph_t g2 = nullptr;
+    cudaStreamEndCapture(b->cap, &g2);
+    if (g2) cudaGraphDestroy(g2);
+    cudaGetLastError();
+    throw;
+  }
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+  size_t nnodes = 0;
+  cudaGraphGetNodes(graph, nullptr, &nnodes);
+  cudaGraphDestroy(graph);
+  CUDA_OK(e);
+  ++b->captures;
+  b->last_nodes = (long long)nnodes;
+  b->graphs.push_back({side, mask, exec, (long long)nnodes});
+}
+
+void batch_release(ccsd_batch_ctx* b) {
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  b->graphs.clear();
+  for (size_t s = 0; s < b->sys.size(); ++s) {
+    ccsd_ctx* c = b->sys[s];
+    cudaStreamSynchronize(c->st);
+    c->st = b->orig[s];
+    c->ex->set_stream(b->orig[s]);
+  }
+  for (cudaStream_t st : b->own) cudaStreamDestroy(st);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  b->own.clear();
+  b->join.clear();
+  b->fork = nullptr;
+  b->cap = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+ccsd_status ccsd_batch_create(int nsys, const ccsd_handle* systems, int nvec, ccsd_batch* out) {
+  if (!out) return CCSD_ERR_ARG;
+  *out = nullptr;
+  if (nsys < 1 || !systems || nvec < 1 || nvec > 16) return CCSD_ERR_ARG;
+  for (int s = 0; s < nsys; ++s) {
+    if (!systems[s]) return CCSD_ERR_ARG;
+    for (int r = 0; r < s; ++r)
+      if (systems[r] == systems[s]) return CCSD_ERR_ARG;
+  }
+  std::unique_ptr<ccsd_batch_ctx> b(new ccsd_batch_ctx);
+  b->nvec = nvec;
+  ccsd_status st = batch_guarded(b.get(), [&] {
+    CUDA_OK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    CUDA_OK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+    for (int s = 0; s < nsys; ++s) {
+      ccsd_ctx* c = systems[s];
+      cudaStream_t st = nullptr;
+      CUDA_OK(cudaStreamSynchronize(c->st));
+      CUDA_OK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      cudaEvent_t e = nullptr;
+      CUDA_OK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      b->own.push_back(st);
+      b->join.push_back(e);
+      b->orig.push_back(c->st);
+      b->sys.push_back(c);
+      c->st = st;
+      c->ex->set_stream(st);
+      b->X.emplace_back(new DevBuf(nvec * c->dim));
+      b->Y.emplace_back(new DevBuf(nvec * c->dim));
+      CUDA_OK(cudaMemsetAsync(b->X.back()->p, 0, nvec * c->dim * sizeof(double), st));
+      b->W.emplace_back(nullptr);
+      b->G.emplace_back(nullptr);
+    }
+  });
+  if (st != CCSD_OK) {
+    batch_release(b.get());
+    return st;
+  }
+  *out = b.release();
+  return CCSD_OK;
+}
+
+ccsd_status ccsd_batch_transform(ccsd_batch b, int side, const double* const* x, double* const* y) {
+  return batch_guarded(b, [&] {
+    if ((side != 0 && side != 1) || !x || !y) throw Err(CCSD_ERR_ARG, "bad arguments");
+    const int ns = (int)b->sys.size();
+    for (int s = 0; s < ns; ++s) {
+      if (!x[s] || !y[s]) throw Err(CCSD_ERR_ARG, "null vector array");
+      if (!b->sys[s]->have_ground) throw Err(CCSD_ERR_STATE, "a system has no amplitudes");
+    }
+    for (int s = 0; s < ns; ++s) {
+      ccsd_ctx* c = b->sys[s];
+      CUDA_OK(cudaMemcpyAsync(b->X[s]->p, x[s], b->nvec * c->dim * sizeof(double), cudaMemcpyDefault, c->st));
+      CUDA_OK(cudaStreamSynchronize(c->st));
+    }
+    batch_run(b, side, std::vector<char>(ns, 1));
+    for (int s = 0; s < ns; ++s) {
+      ccsd_ctx* c = b->sys[s];
+      CUDA_OK(cudaMemcpyAsync(y[s], b->Y[s]->p, b->nvec * c->dim * sizeof(double), cudaMemcpyDefault, c->st));
+    }
+    for (int s = 0; s < ns; ++s) CUDA_OK(cudaStreamSynchronize(b->sys[s]->st));
+  });
+}
+
+ccsd_status ccsd_batch_eom_solve(ccsd_batch b, int side, int nroots, double* omega, int* iters) {
+  return batch_guarded(b, [&] {
+    const int ns = (int)b->sys.size();
+    if ((side != 0 && side != 1) || nroots < 1 || nroots > b->nvec) throw Err(CCSD_ERR_ARG, "bad arguments");
+    for (ccsd_ctx* c : b->sys) {
+      if (nroots > c->n1) throw Err(CCSD_ERR_ARG, "nroots exceeds a system's singles dimension");
+      if (!c->have_ground) throw Err(CCSD_ERR_STATE, "a system has no ground state");
+      if (side == 1 && (!c->have_right || (int)c->omega.size() != nroots))
+        throw Err(CCSD_ERR_STATE, "side 1 needs the right solve with the same nroots first");
+    }
+    std::vector<std::unique_ptr<Davidson>> d(ns);
+    for (int s = 0; s < ns; ++s) {
+      ccsd_ctx* c = b->sys[s];
+      const double tol = refining(c) ? std::max(c->opt.tol_eom, 10.0 * c->opt.tol_switch) : c->opt.tol_eom;
+      d[s].reset(new Davidson(c, side, nroots, tol, side == 1 ? &c->R : nullptr));
+      if (side == 1) d[s]->targets = c->omega;
+    }
+    std::vector<char> done(ns, 0), mask(ns, 1);
+    std::vector<int> it(ns, 0);
+    int left = ns;
+    while (left > 0) {
+      // transform every pending vector, nvec per system and launch
+      std::vector<int> off(ns, 0);
+      for (;;) {
+        bool any = false;
+        std::vector<int> k(ns, 0);
+        for (int s = 0; s < ns; ++s) {
+          if (!mask[s]) continue;
+          ccsd_ctx* c = b->sys[s];
+          if (!done[s]) k[s] = std::max(0, std::min(b->nvec, d[s]->count - off[s]));
+          if (k[s] > 0) {
+            any = true;
+            CUDA_OK(cudaMemcpyAsync(b->X[s]->p, d[s]->vin(off[s]), k[s] * c->dim * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, c->st));
+          }
+          if (k[s] < b->nvec)
+            CUDA_OK(cudaMemsetAsync(b->X[s]->p + k[s] * c->dim, 0, (b->nvec - k[s]) * c->dim * sizeof(double),
+                                    c->st));
+          CUDA_OK(cudaStreamSynchronize(c->st));
+        }
+        if (!any) break;
+        batch_run(b, side, mask);
+        for (int s = 0; s < ns; ++s)
+          if (k[s] > 0) {
+            ccsd_ctx* c = b->sys[s];
+            CUDA_OK(cudaMemcpyAsync(d[s]->vout(off[s]), b->Y[s]->p, k[s] * c->dim * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, c->st));
+            off[s] += k[s];
+          }
+      }
+      for (int s = 0; s < ns; ++s) {
+        if (done[s]) continue;
+        CUDA_OK(cudaStreamSynchronize(b->sys[s]->st));
+        if (d[s]->advance()) {
+          done[s] = 1;
+          --left;
+        }
+      }
+      // drop converged systems from the launched set once a quarter of it is idle
+      int active = 0, idle = 0;
+      for (int s = 0; s < ns; ++s)
+        if (mask[s]) (done[s] ? idle : active)++;
+      if (active > 0 && 4 * idle >= active + idle)
+        for (int s = 0; s < ns; ++s)
+          if (done[s]) mask[s] = 0;
+    }
+    for (int s = 0; s < ns; ++s) {
+      ccsd_ctx* c = b->sys[s];
+      std::vector<double> w = d[s]->omega;
+      int its = d[s]->iterations;
+      std::vector<std::unique_ptr<DevBuf>> vecs;
+      d[s]->results(vecs);
+      d[s].reset();
+      if (refining(c)) {  // FP64 continuation of this system alone
+        PrecScope fp64(c, CCSD_PREC_FP64);
+        std::vector<std::unique_ptr<DevBuf>> fin;
+        const std::vector<double> wm = w;
+        its += davidson(c, side, nroots, w, fin, c->opt.tol_eom, &vecs, &wm);
+        vecs.swap(fin);
+      }
+      if (side == 0) {
+        c->R.swap(vecs);
+        finish_right(c, w);
+      } else {
+        finish_left(c, w, vecs);
+      }
+      if (omega) std::copy(w.begin(), w.end(), omega + (size_t)s * nroots);
+      if (iters) iters[s] = its;
+    }
+  });
+}
+
+ccsd_status ccsd_batch_stats(ccsd_batch b, long long* launches, long long* captures, long long* nodes) {
+  if (!b) return CCSD_ERR_ARG;
+  if (launches) *launches = b->launches;
+  if (captures) *captures = b->captures;
+  if (nodes) *nodes = b->last_nodes;
+  return CCSD_OK;
+}
+
+const char* ccsd_batch_last_error(ccsd_batch b) { return b ? b->err.c_str() : "null batch"; }
+
+void ccsd_batch_destroy(ccsd_batch b) {
+  if (!b) return;
+  batch_release(b);
+  delete b;
 }
 
 }  // extern "C"

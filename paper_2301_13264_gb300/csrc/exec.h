@@ -10,7 +10,9 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstdint>
+#include <map>
 #include <set>
 #include <stdexcept>
 #include <string>
@@ -52,6 +54,13 @@ class Executor {
     splits_ = splits;
   }
   int precision() const { return prec_; }
+  void set_stream(cudaStream_t st) { st_ = st; }
+  // While a run is captured into a CUDA graph it must not synchronise: the error
+  // flag of the tensor-core kernels is then read after the graph has run.
+  bool capturing = false;
+  // tensor-core tile choice: 0 = by output width, 1 = time the candidate tile
+  // widths and split counts once per GEMM shape and keep the fastest
+  int autotune = 0;
   // contractions with fewer flops than this stay on the FP64 path in mixed mode
   double tc_min_flops = 2.0e9;
   ExecStats stats;
@@ -119,9 +128,16 @@ class Executor {
   // tcgen05 GEMM on prepared bf16 slices: a [S][Mp][Kp], b [S][Np][Kp] (rows and K
   // zero-padded; Mp a multiple of 128, Np of the tile width chosen for N);
   // C[m*sCm + n*sCn] = alpha * sum + beta * C.
+  // BN (tile width, 0: by N) and nsplit (split-K count, 0: heuristic) may be given.
   void tc_run(const void* a, int64_t Mp, const void* b, int64_t Np, int K, int64_t Kp, int S, int M, int N, double* C,
               int64_t sCm, int64_t sCn, double alpha, double beta, const Strided* om = nullptr,
-              const Strided* on = nullptr);
+              const Strided* on = nullptr, int BN = 0, int nsplit = 0);
+  struct TcChoice {
+    int bn, nsplit;  // nsplit 0: heuristic
+  };
+  // tile width and split count for a tensor-core GEMM shape (timed once per shape when autotune is on)
+  TcChoice tc_choice(int M, int N, int64_t Kp, int S, bool strided);
+  std::map<std::array<int64_t, 4>, TcChoice> tc_tuned_;
   // pp-ladder contractions against the bare vvvv tensor (ladder.cu); false if op is not one
   bool try_ladder(const Op& op);
   int ladder_w_ = -1;  // tensor id of W[a][b][c][d] = (ac|bd)
@@ -135,6 +151,12 @@ class Executor {
   };
   std::vector<WPM> wpm_;
   void* pairs_ = nullptr;
+  struct LadderTables {
+    std::vector<int64_t> offA, offIJ, offJI;
+    std::vector<unsigned char> same;
+    void* dev;
+  };
+  std::vector<LadderTables> ladder_tables_;
   // value of the device error flag (synchronises the stream); 0 when no tensor-core kernel ran
   int tc_error();
   // tensors whose values never change after set-up (their bf16 slices may be cached)

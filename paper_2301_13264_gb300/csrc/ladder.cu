@@ -311,21 +311,30 @@ bool Executor::try_ladder(const Op& op) {
   const bool mixed = (prec_ == PREC_MIXED && flops_each >= tc_min_flops);
   const int2* pairs = pair_table();
   const double* Wp = ts_[ladder_w_].p;
-  // row tables of the pair-symmetric form (device copies, freed stream-ordered)
-  void* tables = nullptr;
+  // row tables of the pair-symmetric form: device copies kept for the executor's
+  // life (one per distinct table), so that a run issues no host-to-device copy
   const int64_t* dOffA = nullptr;
   const int64_t* dOffIJ = nullptr;
   const int64_t* dOffJI = nullptr;
   const unsigned char* dSame = nullptr;
   if (sym) {
     const size_t n8 = offA.size() * sizeof(int64_t);
-    if (cudaMallocAsync(&tables, 3 * n8 + same.size() + 16, st_) != cudaSuccess)
-      throw std::runtime_error("ladder row tables: out of memory");
-    char* base = (char*)tables;
-    cudaMemcpyAsync(base, offA.data(), n8, cudaMemcpyHostToDevice, st_);
-    cudaMemcpyAsync(base + n8, offIJ.data(), n8, cudaMemcpyHostToDevice, st_);
-    cudaMemcpyAsync(base + 2 * n8, offJI.data(), n8, cudaMemcpyHostToDevice, st_);
-    cudaMemcpyAsync(base + 3 * n8, same.data(), same.size(), cudaMemcpyHostToDevice, st_);
+    const LadderTables* tab = nullptr;
+    for (const LadderTables& t : ladder_tables_)
+      if (t.offA == offA && t.offIJ == offIJ && t.offJI == offJI && t.same == same) tab = &t;
+    if (!tab) {
+      LadderTables t{offA, offIJ, offJI, same, nullptr};
+      if (cudaMalloc(&t.dev, 3 * n8 + same.size() + 16) != cudaSuccess)
+        throw std::runtime_error("ladder row tables: out of memory");
+      char* base = (char*)t.dev;
+      cudaMemcpy(base, offA.data(), n8, cudaMemcpyHostToDevice);
+      cudaMemcpy(base + n8, offIJ.data(), n8, cudaMemcpyHostToDevice);
+      cudaMemcpy(base + 2 * n8, offJI.data(), n8, cudaMemcpyHostToDevice);
+      cudaMemcpy(base + 3 * n8, same.data(), same.size(), cudaMemcpyHostToDevice);
+      ladder_tables_.push_back(std::move(t));
+      tab = &ladder_tables_.back();
+    }
+    const char* base = (const char*)tab->dev;
     dOffA = (const int64_t*)base;
     dOffIJ = (const int64_t*)(base + n8);
     dOffJI = (const int64_t*)(base + 2 * n8);
@@ -474,7 +483,6 @@ bool Executor::try_ladder(const Op& op) {
                                                           op.alpha);
   tmp_free(Yp);
   tmp_free(Ym);
-  if (tables) cudaFreeAsync(tables, st_);
   stats.ladders++;
   return true;
 }

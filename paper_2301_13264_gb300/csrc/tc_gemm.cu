@@ -416,6 +416,8 @@ void Executor::clear_cache() {
     cudaFree(pairs_);
     pairs_ = nullptr;
   }
+  for (LadderTables& t : ladder_tables_) cudaFree(t.dev);
+  ladder_tables_.clear();
   cache_bytes_ = 0;
   if (tc_err_) {
     cudaFree(tc_err_);
@@ -477,10 +479,11 @@ bool Executor::tc_contract(int M, int N, int K, const double* A, const Strided& 
     std::swap(sCm, sCn);
     std::swap(om, on);
   }
-  const int BN = (N > 128) ? 256 : (N > 64 ? 128 : 64);
   const int S = (splits_ >= 3) ? 3 : 2;
   const int64_t Kp = ((int64_t)K + tc::BK - 1) / tc::BK * tc::BK;
   const int64_t Mp = ((int64_t)M + tc::BM - 1) / tc::BM * tc::BM;
+  const TcChoice ch = tc_choice(M, N, Kp, S, om && on);
+  const int BN = ch.bn;
   const int64_t Np = ((int64_t)N + BN - 1) / BN * BN;
   if (Np / BN > 65535) return false;
   if (!tc_err_) {
@@ -507,17 +510,89 @@ bool Executor::tc_contract(int M, int N, int K, const double* A, const Strided& 
   bool ownA = false, ownB = false;
   __nv_bfloat16* a = get(A, ag, M, Mp, a_const, ownA);
   __nv_bfloat16* b = get(B, bg, N, Np, b_const, ownB);
-  tc_run(a, Mp, b, Np, K, Kp, S, M, N, C, sCm, sCn, alpha, beta, om, on);
+  tc_run(a, Mp, b, Np, K, Kp, S, M, N, C, sCm, sCn, alpha, beta, om, on, BN, ch.nsplit);
   if (ownA) cudaFreeAsync(a, st_);
   if (ownB) cudaFreeAsync(b, st_);
   return true;
 }
 
+static int tile_width(int N) { return (N > 128) ? 256 : (N > 64 ? 128 : 64); }
+
+// split-K count that fills the machine when the output has few tiles
+static int split_count(int64_t tiles, int iters) {
+  int nsplit = 1;
+  if (tiles < 148 && iters >= 32) nsplit = (int)std::min<int64_t>(std::min<int64_t>(296 / tiles, iters / 16), 64);
+  return std::max(nsplit, 1);
+}
+
+Executor::TcChoice Executor::tc_choice(int M, int N, int64_t Kp, int S, bool strided) {
+  TcChoice ch{tile_width(N), 0};
+  if (!autotune) return ch;
+  const std::array<int64_t, 4> key{M, N, Kp, S * 2 + (strided ? 1 : 0)};
+  auto it = tc_tuned_.find(key);
+  if (it != tc_tuned_.end()) return it->second;
+  if (capturing) return ch;  // shapes are tuned in an uncaptured run first
+  // candidates: tile widths up to twice the output width, split counts around the heuristic
+  const int64_t Mp = ((int64_t)M + tc::BM - 1) / tc::BM * tc::BM;
+  const int64_t Nmax = ((int64_t)N + 255) / 256 * 256;
+  void *a = nullptr, *b = nullptr;
+  double* C = nullptr;
+  const size_t abytes = (size_t)S * Mp * Kp * 2, bbytes = (size_t)S * Nmax * Kp * 2;
+  if (cudaMalloc(&a, abytes) != cudaSuccess || cudaMalloc(&b, bbytes) != cudaSuccess ||
+      cudaMalloc((void**)&C, (size_t)M * N * sizeof(double)) != cudaSuccess) {
+    cudaFree(a);
+    cudaFree(b);
+    cudaGetLastError();
+    return ch;  // no room to tune: keep the heuristic
+  }
+  cudaMemsetAsync(a, 0, abytes, st_);
+  cudaMemsetAsync(b, 0, bbytes, st_);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int nprod = (S == 2) ? 3 : 6;
+  const int iters = nprod * (int)(Kp / tc::BK);
+  float best = 1e30f;
+  for (int bn : {64, 128, 256}) {
+    if (bn > 64 && bn >= 2 * N) continue;
+    const int64_t Np = ((int64_t)N + bn - 1) / bn * bn;
+    const int64_t tiles = (Mp / tc::BM) * (Np / bn);
+    const int h = split_count(tiles, iters);
+    std::vector<int> splits{1, h, std::min(2 * h, std::max(1, iters / 4))};
+    if (tiles < 152 && iters >= 8) splits.push_back(std::max(1, std::min<int>(152 / (int)tiles, iters / 4)));
+    std::sort(splits.begin(), splits.end());
+    splits.erase(std::unique(splits.begin(), splits.end()), splits.end());
+    for (int ns : splits) {
+      if (ns > 64) continue;
+      tc_run(a, Mp, b, Np, (int)Kp, Kp, S, M, N, C, N, 1, 1.0, 0.0, nullptr, nullptr, bn, ns);  // warm
+      cudaEventRecord(e0, st_);
+      for (int r = 0; r < 3; ++r)
+        tc_run(a, Mp, b, Np, (int)Kp, Kp, S, M, N, C, N, 1, 1.0, 0.0, nullptr, nullptr, bn, ns);
+      cudaEventRecord(e1, st_);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        ch = TcChoice{bn, ns};
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(st_);
+  cudaFree(a);
+  cudaFree(b);
+  cudaFree(C);
+  tc_tuned_[key] = ch;
+  return ch;
+}
+
 void Executor::tc_run(const void* a, int64_t Mp, const void* b, int64_t Np, int K, int64_t Kp, int S, int M, int N,
                       double* C, int64_t sCm, int64_t sCn, double alpha, double beta, const Strided* om,
-                      const Strided* on) {
+                      const Strided* on, int BN, int nsplit_req) {
   (void)K;
-  const int BN = (N > 128) ? 256 : (N > 64 ? 128 : 64);
+  if (BN == 0) BN = tile_width(N);
   if (Np % BN != 0 || Mp % tc::BM != 0 || Np / BN > 65535) throw std::runtime_error("tc_run: bad padding");
   if (!tc_err_) {
     if (cudaMalloc(&tc_err_, sizeof(int)) != cudaSuccess) throw std::runtime_error("tc flag allocation failed");
@@ -539,9 +614,7 @@ void Executor::tc_run(const void* a, int64_t Mp, const void* b, int64_t Np, int 
   }
   const int iters = p.nprod * p.kt_per_prod;
   const int64_t tiles = (Mp / tc::BM) * (Np / BN);
-  int nsplit = 1;
-  if (tiles < 148 && iters >= 32) nsplit = (int)std::min<int64_t>(std::min<int64_t>(296 / tiles, iters / 16), 64);
-  nsplit = std::max(nsplit, 1);
+  int nsplit = nsplit_req > 0 ? std::min(nsplit_req, iters) : split_count(tiles, iters);
   p.it_per_split = (iters + nsplit - 1) / nsplit;
   nsplit = (iters + p.it_per_split - 1) / p.it_per_split;
   p.C = C;
