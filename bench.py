@@ -27,6 +27,10 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "Jacobian transforms/s and time-to-converged coupling at o=33,v=228 vs FP64 GPU form"
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
+# DRAM bytes (read + write) of one ladder GEMM-pair launch, from an ncu capture
+# (profiles/k_tc_gemm_ladder_thymine_adz.md), keyed by (workload, nvec, products)
+LADDER_TRAFFIC = {}
 UNIT = "transforms/s"
 
 
@@ -300,9 +304,17 @@ def run_ours(args, rank, world, local_rank):
     achieved = ladder_alg / (lad_ms * 1e-3) / 1e12 if lad_ms > 0 else 0.0
     issued = prof["ladder_issued_flops"] / n_ladder / (lad_ms * 1e-3) / 1e12 if lad_ms > 0 else 0.0
     executed = prof["ladder_flops"] / n_ladder / (lad_ms * 1e-3) / 1e12 if lad_ms > 0 else 0.0
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_tc_gemm<256> (pp-ladder, +/- GEMM pair)",
-                "peak_source": f"bf16_tflops_sustained of {src} MEASURED_PEAKS.json",
+    # the split arithmetic issues nprod bf16 products per FP64-equivalent multiply-add,
+    # so its peak is the bf16 peak / nprod (FP64 DFMA path: the FP64 peak)
+    nprod = (3 if args.splits == 2 else 6) if prec == B.PREC_MIXED else 1
+    peak_split = peak / nprod if prec == B.PREC_MIXED else FP64_PEAK_TFLOPS
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_split, "unit": "TFLOP/s",
+                "frac": achieved / peak_split, "traffic": LADDER_TRAFFIC.get((args.workload, args.nvec, nprod)),
+                "kernel": "k_tc_gemm<256> (pp-ladder, +/- GEMM pair)",
+                "peak_source": (f"bf16_tflops_sustained of {src} MEASURED_PEAKS.json / {nprod} bf16 products per "
+                                "FP64-equivalent multiply-add (split-bf16 arithmetic)") if prec == B.PREC_MIXED
+                else "FP64 DFMA peak: 152 SMs x 2.07 GHz x 4 flop/clk",
+                "peak_bf16": peak, "frac_of_bf16_peak": achieved / peak,
                 "algorithmic_flops_per_launch": ladder_alg,
                 "algorithmic_definition": "o^2 v^4 / 4 multiply-adds per vector (pair-packed ladder) x nvec",
                 "executed_tflops": executed, "issued_tflops": issued, "issued_frac": issued / peak,

@@ -52,7 +52,7 @@ typedef enum {
   CCSD_ERR_NOT_CONVERGED = 5, /* iteration limit reached */
   CCSD_ERR_COMPLEX_ROOT = 6,  /* a wanted EOM root came out complex (defective intersection) */
   CCSD_ERR_DEGENERATE = 7,    /* omega_l - omega_k below the degeneracy threshold */
-  CCSD_ERR_NOT_HF = 8,        /* reserved: relaxed-orbital mode needs an HF reference */
+  CCSD_ERR_NOT_HF = 8,        /* relax_orbitals = 1 without Hartree-Fock orbitals (F_ia != 0) */
   CCSD_ERR_TIMEOUT = 9        /* a device-side wait exceeded its budget */
 } ccsd_status;
 
@@ -62,7 +62,9 @@ enum { CCSD_GUESS_MP2 = 0 };
 typedef struct {
   int precision;        /* CCSD_PREC_FP64 or CCSD_PREC_MIXED (tensor-core split products) */
   int splits;           /* mixed mode: bf16 slices per FP64 operand (2 or 3) */
-  int relax_orbitals;   /* must be 0: orbitals are fixed and x-independent */
+  int relax_orbitals;   /* 0: orbitals fixed and x-independent (unrelaxed coupling); 1: Hartree-Fock
+                           orbitals that follow x (Eq. orbitalrelax): the inputs must be Hartree-Fock
+                           orbitals (ccsd_scf), else ccsd_create returns CCSD_ERR_NOT_HF */
   double tol_res;       /* ground state: max |Omega| */
   double tol_eom;       /* EOM: packed residual norm */
   double tol_lin;       /* Lambda and zeta equations: max |residual| */
@@ -131,15 +133,39 @@ ccsd_status ccsd_get_states(ccsd_handle h, int nroots, double* r0, double* right
 
 /* Coupling densities for the pair (k, l), k != l: the gradient with respect
  * to (h, B) of the Lagrangian's Hamiltonian-dependent part, so that
- * F_kl^x = sum_pq D_pq dh_pq + sum_Jpq Z_Jpq dB_Jpq (Eq. NAC_NC; the orbital
- * term vanishes because the orbitals are fixed).  D[n*n], Z[naux*n*n] outputs
- * (Z may be NULL).  Solves the zeta equations of Eq. amplituderelax (or uses
- * the closed form for l = 0). */
+ * F_kl^x = sum_pq D_pq dh_pq + sum_Jpq Z_Jpq dB_Jpq (Eq. NAC_NC).  D[n*n],
+ * Z[naux*n*n] outputs (Z may be NULL).  Solves the zeta equations of Eq.
+ * amplituderelax (or uses the closed form for l = 0).  With relax_orbitals = 1
+ * the densities also carry the orbital term kappa-bar_ai F^x_ai: kappa-bar solves
+ * kappa-bar^T A^HF = -(k-eta)^T (Eq. orbitalrelax) by conjugate gradients, with
+ * k-eta = D_ai - D_ia of the pair's one-electron transition density plus the
+ * derivative of the amplitude and excited-state conditions along each
+ * occupied-virtual orbital rotation; F^x is the derivative of the Fock matrix
+ * along (dh, dB), and dh, dB must be given in the Hartree-Fock orbitals of the
+ * handle (ccsd_rotate_integrals). */
 ccsd_status ccsd_coupling_densities(ccsd_handle h, int k, int l, double* D, double* Z);
 
 /* F[d] = F_kl^x along ndir directions: dh[d][n*n], dB[d][naux*n*n]. */
 ccsd_status ccsd_derivative_coupling(ccsd_handle h, int k, int l, int ndir, const double* dh, const double* dB,
                                      double* F);
+
+/* ---- Hartree-Fock orbitals (relaxed mode) -------------------------------------
+ * The nearest Hartree-Fock orbitals to the given orthonormal ones: U = exp(K) with
+ * K[a][i] = kappa[i][a] = -K[i][a] (occupied-virtual rotations only), kappa solving
+ * F(U^T h U, U^T B U)_ia = 0 (closed-shell Fock matrix, Lagrangian section) by
+ * Newton-type steps (A^HF d-kappa = -F' at the current orbitals, conjugate
+ * gradients, preconditioner 1/(eps_a - eps_i)) until max |F'_ia| < tol.  Returns
+ * U[n*n] and, when not NULL, the rotated integrals h_out[n*n], B_out[naux*n*n].
+ * Arrays may be host or device memory.  CCSD_ERR_NOT_CONVERGED after 100 steps. */
+ccsd_status ccsd_scf(const double* eps, const double* h, const double* B, int o, int v, int naux, double tol,
+                     double* U_out, double* h_out, double* B_out, int* iters);
+/* h_out = U^T h U, B_out^J = U^T B^J U (e.g. a perturbation direction taken to the
+ * Hartree-Fock orbitals). */
+ccsd_status ccsd_rotate_integrals(const double* U, const double* h, const double* B, int o, int v, int naux,
+                                  double* h_out, double* B_out);
+/* kappa-bar[o*v] ([i][a]) of the pair (k, l) (relax_orbitals = 1 only; computes the pair's
+ * densities if needed). */
+ccsd_status ccsd_get_orbital_multipliers(ccsd_handle h, int k, int l, double* kbar);
 
 /* ---- learned initial guess for the doubles amplitudes ---------------------
  * A 3 -> 128 -> 128 -> 1 MLP (tanh hidden layers) maps per-element features
@@ -252,7 +278,8 @@ const char* ccsd_last_error(ccsd_handle h);
 void ccsd_destroy(ccsd_handle h);
 
 /* Host-only: text description of one of the library's tensor programs
- * ("fwd", "jvp", "vjp", "hvp", "dens1", "dens0").  Writes at most len bytes
+ * ("fwd", "jvp", "vjp", "hvp", "dens1", "dens0", and the orbital-relaxation programs
+ * "hf_fock", "hf_A", "hf_rotT", "hf_kdens", "hf_rotate").  Writes at most len bytes
  * (NUL-terminated) and returns the full length needed (without the NUL), or
  * -1 for an unknown name.  Touches no GPU. */
 long long ccsd_describe_program(const char* which, char* buf, size_t len);

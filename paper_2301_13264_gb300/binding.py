@@ -378,3 +378,33 @@ def ccsd_batch_stats(b):
 def ccsd_batch_destroy(b):
     if b:
         _batch_fn("ccsd_batch_destroy", [_P], None)(b)
+
+
+# ---- Hartree-Fock orbitals (relaxed mode) -------------------------------------
+
+def ccsd_scf(eps, h, B, o, v, naux, tol=1e-12, rotated=True):
+    """Nearest Hartree-Fock orbitals: (U[n,n], h'[n,n], B'[naux,n,n], iterations) as numpy arrays."""
+    n = o + v
+    U = np.zeros((n, n))
+    hr = np.zeros((n, n)) if rotated else None
+    Br = np.zeros((naux, n, n)) if rotated else None
+    it = ctypes.c_int()
+    f = _mlp_fn("ccsd_scf", [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _P, _P, _P,
+                             ctypes.POINTER(ctypes.c_int)])
+    _check(None, f(_ptr(eps), _ptr(h), _ptr(B), o, v, naux, tol, _ptr(U), _ptr(hr), _ptr(Br), ctypes.byref(it)))
+    return U, hr, Br, it.value
+
+
+def ccsd_rotate_integrals(U, h, B, o, v, naux):
+    n = o + v
+    hr, Br = np.zeros((n, n)), np.zeros((naux, n, n))
+    f = _mlp_fn("ccsd_rotate_integrals", [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P])
+    _check(None, f(_ptr(U), _ptr(h), _ptr(B), o, v, naux, _ptr(hr), _ptr(Br)))
+    return hr, Br
+
+
+def ccsd_get_orbital_multipliers(h, k, l, o, v):
+    kb = np.zeros((o, v))
+    f = _mlp_fn("ccsd_get_orbital_multipliers", [_P, ctypes.c_int, ctypes.c_int, _P])
+    _check(h, f(h, k, l, _ptr(kb)))
+    return kb

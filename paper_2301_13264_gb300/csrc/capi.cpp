@@ -7,6 +7,8 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -18,6 +20,7 @@
 #include "exec.h"
 #include "kernels.cuh"
 #include "mlp.h"
+#include "orbital.h"
 #include "programs.h"
 #include "small_linalg.h"
 
@@ -91,6 +94,10 @@ struct ccsd_ctx {
   DevBuf Dd, Zd;
   long long prof_launch0 = 0;
   DevBuf guess_model;  // MLP model (floats) for the starting doubles, or empty
+  // orbital relaxation (relax_orbitals): Hartree-Fock programs on the handle's (h, B)
+  std::unique_ptr<HFPrograms> hfp;
+  std::unique_ptr<Executor> hx;
+  std::vector<double> kbar;  // kappa-bar of the last pair [o][v]
 };
 
 namespace {
@@ -597,6 +604,28 @@ int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std:
   return d.iterations;
 }
 
+int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol);
+
+// FP64 refinement of mixed-precision eigenpairs (w, vecs) to tol_eom: defect
+// correction root by root, falling back to an FP64 Davidson continuation that
+// follows the same roots if a correction stalls.  Returns the transforms used.
+int refine_roots(ccsd_ctx* c, int side, std::vector<double>& w, std::vector<std::unique_ptr<DevBuf>>& vecs) {
+  const int nroots = (int)w.size();
+  int n = 0;
+  try {
+    for (int k = 0; k < nroots; ++k) n += refine_eigenpair(c, side, vecs[k]->p, w[k], c->opt.tol_eom);
+    return n;
+  } catch (const Err& e) {
+    if (e.code != CCSD_ERR_NOT_CONVERGED) throw;
+  }
+  PrecScope fp64(c, CCSD_PREC_FP64);
+  const std::vector<double> wm = w;
+  std::vector<std::unique_ptr<DevBuf>> fin;
+  n += davidson(c, side, nroots, w, fin, c->opt.tol_eom, &vecs, &wm);
+  vecs.swap(fin);
+  return n;
+}
+
 // Davidson to tol_eom; in mixed mode with refinement the mixed-precision solution
 // (to 10 tol_switch) seeds an FP64 continuation that follows the same roots.
 int davidson_refined(ccsd_ctx* c, int side, int nroots, std::vector<double>& w,
@@ -604,12 +633,86 @@ int davidson_refined(ccsd_ctx* c, int side, int nroots, std::vector<double>& w,
                      const std::vector<std::unique_ptr<DevBuf>>* init = nullptr,
                      const std::vector<double>* targets = nullptr) {
   if (!refining(c)) return davidson(c, side, nroots, w, out, c->opt.tol_eom, init, targets);
+  static const bool verbose = [] {
+    const char* e = getenv("CCSD_VERBOSE");
+    return e && e[0] == '1';
+  }();
+  auto t0 = std::chrono::steady_clock::now();
   std::vector<std::unique_ptr<DevBuf>> mixed;
-  int it = davidson(c, side, nroots, w, mixed, std::max(c->opt.tol_eom, 10.0 * c->opt.tol_switch), init, targets);
-  PrecScope fp64(c, CCSD_PREC_FP64);
-  const std::vector<double> wm = w;
-  it += davidson(c, side, nroots, w, out, c->opt.tol_eom, &mixed, &wm);
-  return it;
+  const int it1 = davidson(c, side, nroots, w, mixed, std::max(c->opt.tol_eom, 10.0 * c->opt.tol_switch), init,
+                           targets);
+  auto t1 = std::chrono::steady_clock::now();
+  const int it2 = refine_roots(c, side, w, mixed);
+  out.swap(mixed);
+  if (verbose) {
+    auto t2 = std::chrono::steady_clock::now();
+    fprintf(stderr, "[davidson side %d] mixed phase %d iterations %.2f s, FP64 refinement %d transforms %.2f s\n",
+            side, it1, std::chrono::duration<double>(t1 - t0).count(), it2,
+            std::chrono::duration<double>(t2 - t1).count());
+  }
+  return it1 + it2;
+}
+
+// Defect correction of one eigenpair (x, w) of A (side 0) or A^T (side 1) to the FP64
+// residual tolerance: per outer step one FP64 transform gives r = A x - w x (w the
+// Rayleigh quotient of the unit vector x); the correction d (d perpendicular to x)
+// solves the projected equation P (A - w) P d = -r, P = 1 - x x^T, by preconditioned
+// Jacobi + DIIS with transforms at the handle's (mixed) precision, to 1e-3 of |r|;
+// x += d.  Each step gains the mixed operator's accuracy (~5 digits), so two or three
+// FP64 transforms per root replace an FP64 Davidson continuation.  Returns the number
+// of transforms (FP64 + mixed); throws if the residual stops decreasing.
+int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol) {
+  const int64_t dim = c->dim;
+  DevBuf ax(dim), r(dim), d(dim), ad(dim), res(dim), dn(dim);
+  auto transform = [&](const double* in, double* out) {
+    if (side == 0)
+      right_block(c, in, out, 1);
+    else
+      left_block(c, in, out, 1);
+  };
+  auto project = [&](double* v) {  // v -= x <x|v>
+    const double s = gram(c, x, dim, 1, v, dim, 1)[0];
+    launch_axpby(dim, -s, x, 1.0, v, c->st);
+  };
+  int n = 0;
+  double last = 1e300;
+  for (int outer = 0; outer < 8; ++outer) {
+    const double nx = std::sqrt(gram(c, x, dim, 1, x, dim, 1)[0]);
+    launch_axpby(dim, 1.0 / nx, x, 0.0, x, c->st);
+    {
+      PrecScope fp64(c, CCSD_PREC_FP64);
+      transform(x, ax.p);
+    }
+    ++n;
+    w = gram(c, x, dim, 1, ax.p, dim, 1)[0];
+    launch_axpby(dim, 1.0, ax.p, 0.0, r.p, c->st);
+    launch_axpby(dim, -w, x, 1.0, r.p, c->st);
+    const double rn = std::sqrt(std::max(gram(c, r.p, dim, 1, r.p, dim, 1)[0], 0.0));
+    if (rn < tol) return n;
+    if (!(rn < 0.5 * last)) throw Err(CCSD_ERR_NOT_CONVERGED, "eigenpair refinement stalled");
+    last = rn;
+    // inner: P (A - w) P d = -r at the mixed precision
+    launch_precond(c->vs, c->eps.p, r.p, d.p, w, c->st);
+    launch_axpby(dim, 0.0, d.p, -1.0, d.p, c->st);
+    project(d.p);
+    Diis diis(c, c->opt.diis_dim);
+    for (int it = 0; it < 40; ++it) {
+      transform(d.p, ad.p);
+      ++n;
+      launch_axpby(dim, 1.0, ad.p, 0.0, res.p, c->st);
+      launch_axpby(dim, -w, d.p, 1.0, res.p, c->st);
+      project(res.p);
+      launch_axpby(dim, 1.0, r.p, 1.0, res.p, c->st);
+      const double en = std::sqrt(std::max(gram(c, res.p, dim, 1, res.p, dim, 1)[0], 0.0));
+      if (en < 1e-3 * rn) break;
+      launch_precond(c->vs, c->eps.p, res.p, dn.p, w, c->st);
+      launch_axpby(dim, 1.0, d.p, -1.0, dn.p, c->st);  // dn = d - res / (D - w)
+      project(dn.p);
+      diis.step(dn.p, res.p, d.p);
+    }
+    launch_axpby(dim, 1.0, d.p, 1.0, x, c->st);
+  }
+  throw Err(CCSD_ERR_NOT_CONVERGED, "eigenpair refinement did not converge");
 }
 
 // normalise R to unit packed norm, largest-magnitude component positive
@@ -701,6 +804,280 @@ void from_device(ccsd_ctx* c, const double* src, int64_t n, double* dst) {
 const double* left_vec(ccsd_ctx* c, int k) { return k == 0 ? c->lam.p : c->L[k - 1]->p; }
 double omega_of(ccsd_ctx* c, int k) { return k == 0 ? 0.0 : c->omega[k - 1]; }
 
+// ---------------------------------------------------------------------------
+// orbital relaxation (Eq. orbitalrelax and the kappa-bar term of Eq. NAC_NC)
+// ---------------------------------------------------------------------------
+
+// executor of the Hartree-Fock programs, bound to the handle's integrals (FP64)
+Executor& hf_exec(ccsd_ctx* c) {
+  if (!c->hx) {
+    c->hfp.reset(new HFPrograms);
+    build_hf_programs(*c->hfp);
+    c->hx.reset(new Executor(c->hfp->g, c->o, c->v, c->naux, 1, c->st));
+    c->hx->set_precision(CCSD_PREC_FP64, c->opt.splits);
+  }
+  Executor& hx = *c->hx;
+  hx.set_stream(c->st);
+  hx.bind(c->hfp->h, c->h.p);
+  hx.bind(c->hfp->B, c->B.p);
+  hx.bind(c->hfp->ones_o, c->ones.p);
+  return hx;
+}
+
+// max |F_ia| of the handle's integrals
+double fock_ov_max(ccsd_ctx* c) {
+  Executor& hx = hf_exec(c);
+  DevBuf f(c->n1);
+  hx.bind(c->hfp->F, f.p);
+  hx.run(c->hfp->fock);
+  return maxabs(c, f.p, c->n1);
+}
+
+// Solve J x = rhs for J = dF'_ia/dkappa_jb away from a Hartree-Fock point (not symmetric
+// there) by right-preconditioned restarted GMRES(30) on host vectors; J products run in
+// the Hartree-Fock programs.  Used for the steps of ccsd_scf.
+std::vector<double> hf_solve_general(Executor& hx, const HFPrograms& P, int o, int v, cudaStream_t st,
+                                     const std::vector<double>& rhs, const std::vector<double>& eps, double tol,
+                                     int maxit) {
+  const int64_t m = (int64_t)o * v;
+  const int kr = 30;
+  DevBuf xd(m), ad(m), fd(m);
+  std::vector<double> pre(m);
+  for (int i = 0; i < o; ++i)
+    for (int a = 0; a < v; ++a) pre[i * v + a] = 1.0 / std::max(eps[o + a] - eps[i], 1e-3);
+  auto apply = [&](const std::vector<double>& x) {  // J M^-1 x
+    std::vector<double> y(m);
+    for (int64_t i = 0; i < m; ++i) y[i] = pre[i] * x[i];
+    CUDA_OK(cudaMemcpyAsync(xd.p, y.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
+    hx.bind(P.x, xd.p);
+    hx.bind(P.AX, ad.p);
+    hx.bind(P.F, fd.p);
+    hx.run(P.hfA);
+    CUDA_OK(cudaMemcpyAsync(y.data(), ad.p, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_OK(cudaStreamSynchronize(st));
+    return y;
+  };
+  auto nrm = [&](const std::vector<double>& a) {
+    double s = 0.0;
+    for (double q : a) s += q * q;
+    return std::sqrt(s);
+  };
+  std::vector<double> u(m, 0.0);  // solution of J M^-1 u = rhs
+  const double bn = nrm(rhs);
+  if (bn == 0.0) return u;
+  int used = 0;
+  while (used < maxit) {
+    std::vector<double> r = apply(u);
+    ++used;
+    for (int64_t i = 0; i < m; ++i) r[i] = rhs[i] - r[i];
+    double beta = nrm(r);
+    if (beta <= tol * bn) break;
+    std::vector<std::vector<double>> V(1, r);
+    for (double& q : V[0]) q /= beta;
+    std::vector<double> Hm((kr + 1) * kr, 0.0), cs(kr), sn(kr), g(kr + 1, 0.0);
+    g[0] = beta;
+    int k = 0;
+    for (; k < kr && used < maxit; ++k) {
+      std::vector<double> w = apply(V[k]);
+      ++used;
+      for (int j = 0; j <= k; ++j) {
+        double h = 0.0;
+        for (int64_t i = 0; i < m; ++i) h += w[i] * V[j][i];
+        Hm[j * kr + k] = h;
+        for (int64_t i = 0; i < m; ++i) w[i] -= h * V[j][i];
+      }
+      const double hn = nrm(w);
+      Hm[(k + 1) * kr + k] = hn;
+      for (int j = 0; j < k; ++j) {  // previous rotations
+        const double a = Hm[j * kr + k], b = Hm[(j + 1) * kr + k];
+        Hm[j * kr + k] = cs[j] * a + sn[j] * b;
+        Hm[(j + 1) * kr + k] = -sn[j] * a + cs[j] * b;
+      }
+      const double a = Hm[k * kr + k], b = Hm[(k + 1) * kr + k];
+      const double den = std::hypot(a, b);
+      cs[k] = den > 0 ? a / den : 1.0;
+      sn[k] = den > 0 ? b / den : 0.0;
+      Hm[k * kr + k] = den;
+      Hm[(k + 1) * kr + k] = 0.0;
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      if (hn > 0) {
+        for (double& q : w) q /= hn;
+      }
+      V.push_back(w);
+      if (std::fabs(g[k + 1]) <= tol * bn || hn == 0.0) {
+        ++k;
+        break;
+      }
+    }
+    std::vector<double> y(k, 0.0);  // back substitution
+    for (int j = k - 1; j >= 0; --j) {
+      double s = g[j];
+      for (int q = j + 1; q < k; ++q) s -= Hm[j * kr + q] * y[q];
+      y[j] = s / Hm[j * kr + j];
+    }
+    for (int j = 0; j < k; ++j)
+      for (int64_t i = 0; i < m; ++i) u[i] += y[j] * V[j][i];
+  }
+  for (int64_t i = 0; i < m; ++i) u[i] *= pre[i];
+  return u;
+}
+
+// Solve A^HF x = rhs (A^HF symmetric positive definite at a Hartree-Fock minimum) by
+// preconditioned conjugate gradients; A^HF products run in the Hartree-Fock programs,
+// the o*v-sized vectors live on the host.  eps gives the preconditioner 1/(e_a - e_i).
+std::vector<double> hf_solve(Executor& hx, const HFPrograms& P, int o, int v, cudaStream_t st,
+                             const std::vector<double>& rhs, const std::vector<double>& eps, double tol, int maxit) {
+  const int64_t m = (int64_t)o * v;
+  DevBuf xd(m), ad(m), fd(m);
+  auto apply = [&](const std::vector<double>& x) {
+    CUDA_OK(cudaMemcpyAsync(xd.p, x.data(), m * sizeof(double), cudaMemcpyHostToDevice, st));
+    hx.bind(P.x, xd.p);
+    hx.bind(P.AX, ad.p);
+    hx.bind(P.F, fd.p);
+    hx.run(P.hfA);
+    std::vector<double> y(m);
+    CUDA_OK(cudaMemcpyAsync(y.data(), ad.p, m * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CUDA_OK(cudaStreamSynchronize(st));
+    return y;
+  };
+  auto dot = [&](const std::vector<double>& a, const std::vector<double>& b) {
+    double s = 0.0;
+    for (int64_t i = 0; i < m; ++i) s += a[i] * b[i];
+    return s;
+  };
+  std::vector<double> pre(m);
+  for (int i = 0; i < o; ++i)
+    for (int a = 0; a < v; ++a) pre[i * v + a] = 1.0 / std::max(eps[o + a] - eps[i], 1e-3);
+  std::vector<double> x(m, 0.0), r = rhs, z(m), p(m);
+  const double bn = std::sqrt(dot(rhs, rhs));
+  if (bn == 0.0) return x;
+  for (int64_t i = 0; i < m; ++i) z[i] = pre[i] * r[i];
+  p = z;
+  double rz = dot(r, z);
+  for (int it = 0; it < maxit; ++it) {
+    std::vector<double> Ap = apply(p);
+    const double pAp = dot(p, Ap);
+    if (!(pAp > 0.0)) throw Err(CCSD_ERR_NOT_HF, "the Hartree-Fock Hessian is not positive definite");
+    const double alpha = rz / pAp;
+    for (int64_t i = 0; i < m; ++i) {
+      x[i] += alpha * p[i];
+      r[i] -= alpha * Ap[i];
+    }
+    if (std::sqrt(dot(r, r)) <= tol * bn) return x;
+    for (int64_t i = 0; i < m; ++i) z[i] = pre[i] * r[i];
+    const double rz1 = dot(r, z);
+    for (int64_t i = 0; i < m; ++i) p[i] = z[i] + (rz1 / rz) * p[i];
+    rz = rz1;
+  }
+  throw Err(CCSD_ERR_NOT_CONVERGED, "orbital-response equations not converged");
+}
+
+// One-electron transition density D_pq = <psi_k^L| E_pq |psi_l^R> (n x n, device), the
+// derivative of <psi_k^L|H|psi_l^R> with respect to h_pq at fixed states.  Over the
+// reference, singles and doubles,
+//   <psi^L|H|psi^R> = E (l0 r0 + L.R) + l0 eta.R + L.(r0 Omega + A R) + w.Omega,
+// with w_k = <L| tau_k R_1 |HF> (singles of R carried by one more excitation), so D is
+// the h-part of the density programs with seeds z = r0 L + w, g = L, g0 = l0 along R,
+// plus (l0 r0 + L.R) times the energy's own density.
+void transition_density(ccsd_ctx* c, int k, int l, double* D) {
+  const int64_t dim = c->dim, nn = (int64_t)c->n * c->n, nz = (int64_t)c->naux * nn;
+  auto& P = c->P;
+  Executor& ex = *c->ex;
+  const double l0 = (k == 0) ? 1.0 : 0.0;
+  const double* L = left_vec(c, k);
+  DevBuf WL(dim), Zs(nz), e0(1), D2(nn);
+  launch_weight(c->vs, L, WL.p, 1, dim, c->st);
+  if (l == 0) {  // r0 = 1, R = 0: d/dh of l0 E + L.Omega
+    CUDA_OK(cudaMemcpyAsync(e0.p, &l0, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    ex.set_nvec(1);
+    ex.bind(P.eZ1, WL.p);
+    ex.bind(P.eZ2, WL.p + c->n1);
+    ex.bind(P.eE, e0.p);
+    ex.bind(P.eH, D);
+    ex.bind(P.eB, Zs.p);
+    ex.run(P.dens0);
+    sync(c);
+    return;
+  }
+  const double r0 = c->r0[l - 1];
+  const double* R = c->R[l - 1]->p;
+  const double cE = l0 * r0 + gram(c, L, dim, 1, R, dim, 1)[0];
+  DevBuf R1(dim), w(dim), z(dim), Wz(dim), s0(1), zero(dim);
+  CUDA_OK(cudaMemsetAsync(R1.p, 0, dim * sizeof(double), c->st));
+  CUDA_OK(cudaMemcpyAsync(R1.p, R, c->n1 * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  launch_tau_expectation(c->vs, 0.0, L, R1.p, w.p, c->st);
+  CUDA_OK(cudaMemsetAsync(w.p + c->n1, 0, (dim - c->n1) * sizeof(double), c->st));
+  launch_axpby(dim, r0, L, 0.0, z.p, c->st);
+  launch_axpby(dim, 1.0, w.p, 1.0, z.p, c->st);
+  launch_weight(c->vs, z.p, Wz.p, 1, dim, c->st);
+  CUDA_OK(cudaMemcpyAsync(s0.p, &l0, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  ex.set_nvec(1);
+  ex.bind(P.dZ1, Wz.p);
+  ex.bind(P.dZ2, Wz.p + c->n1);
+  ex.bind(P.dG1, WL.p);
+  ex.bind(P.dG2, WL.p + c->n1);
+  ex.bind(P.dG0, s0.p);
+  ex.bind(P.dR1, const_cast<double*>(R));
+  ex.bind(P.dR2, const_cast<double*>(R) + c->n1);
+  ex.bind(P.dH, D);
+  ex.bind(P.dB, Zs.p);
+  ex.run(P.dens1);
+  // + cE dE/dh
+  CUDA_OK(cudaMemsetAsync(zero.p, 0, dim * sizeof(double), c->st));
+  CUDA_OK(cudaMemcpyAsync(e0.p, &cE, sizeof(double), cudaMemcpyHostToDevice, c->st));
+  ex.bind(P.eZ1, zero.p);
+  ex.bind(P.eZ2, zero.p + c->n1);
+  ex.bind(P.eE, e0.p);
+  ex.bind(P.eH, D2.p);
+  ex.bind(P.eB, Zs.p);
+  ex.run(P.dens0);
+  launch_axpby(nn, 1.0, D2.p, 1.0, D, c->st);
+  sync(c);
+}
+
+// With the condition densities of the pair in Dd, Zd: k-eta, kappa-bar, and the
+// kappa-bar densities added to Dd, Zd (so that the coupling contraction carries
+// kappa-bar_ai F^q_ai).
+void add_orbital_relaxation(ccsd_ctx* c, int k, int l) {
+  const int o = c->o, v = c->v, n = c->n;
+  const int64_t nn = (int64_t)n * n, nz = (int64_t)c->naux * nn, m = (int64_t)o * v;
+  PrecScope fp64(c, CCSD_PREC_FP64);
+  DevBuf Dt(nn);
+  transition_density(c, k, l, Dt.p);
+  Executor& hx = hf_exec(c);
+  const HFPrograms& P = *c->hfp;
+  // condition part of k-eta: the adjoint of the rotation map applied to (D, Z)
+  DevBuf xb(m);
+  hx.bind(P.dD, c->Dd.p);
+  hx.bind(P.dZ, c->Zd.p);
+  hx.bind(P.xbar, xb.p);
+  hx.run(P.rotT);
+  std::vector<double> ke(m), Dh(nn), eps(n);
+  CUDA_OK(cudaMemcpyAsync(ke.data(), xb.p, m * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(cudaMemcpyAsync(Dh.data(), Dt.p, nn * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(cudaMemcpyAsync(eps.data(), c->eps.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  sync(c);
+  // overlap part: D_ai - D_ia of the transition density
+  for (int i = 0; i < o; ++i)
+    for (int a = 0; a < v; ++a) ke[i * v + a] += Dh[(int64_t)(o + a) * n + i] - Dh[(int64_t)i * n + o + a];
+  // kappa-bar^T A^HF = -k-eta^T, A^HF symmetric
+  std::vector<double> rhs(m);
+  for (int64_t i = 0; i < m; ++i) rhs[i] = -ke[i];
+  c->kbar = hf_solve(hx, P, o, v, c->st, rhs, eps, 1e-13, 500);
+  // densities of kappa-bar.F, added to the pair's densities
+  DevBuf kb(m), kH(nn), kB(nz), fd(m);
+  CUDA_OK(cudaMemcpyAsync(kb.p, c->kbar.data(), m * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  hx.bind(P.kbar, kb.p);
+  hx.bind(P.F, fd.p);
+  hx.bind(P.kH, kH.p);
+  hx.bind(P.kB, kB.p);
+  hx.run(P.kdens);
+  launch_axpby(nn, 1.0, kH.p, 1.0, c->Dd.p, c->st);
+  launch_axpby(nz, 1.0, kB.p, 1.0, c->Zd.p, c->st);
+  sync(c);
+}
+
 void compute_densities(ccsd_ctx* c, int k, int l) {
   const int nr = (int)c->omega.size();
   if (k < 0 || l < 0 || k == l) throw Err(CCSD_ERR_ARG, "state indices must differ and be >= 0");
@@ -718,9 +1095,12 @@ void compute_densities(ccsd_ctx* c, int k, int l) {
     // zeta = L_k / (E_0 - E_k) = -L_k / omega_k  (Eqs. for the ground-state right state)
     launch_axpby(dim, -1.0 / c->omega[k - 1], c->L[k - 1]->p, 0.0, zeta.p, c->st);
     launch_weight(c->vs, zeta.p, Wz.p, 1, dim, c->st);
+    DevBuf e0(1);
+    CUDA_OK(cudaMemsetAsync(e0.p, 0, sizeof(double), c->st));
     ex.set_nvec(1);
     ex.bind(P.eZ1, Wz.p);
     ex.bind(P.eZ2, Wz.p + c->n1);
+    ex.bind(P.eE, e0.p);
     ex.bind(P.eH, c->Dd.p);
     ex.bind(P.eB, c->Zd.p);
     PrecScope p(c, refining(c) ? CCSD_PREC_FP64 : ex.precision());
@@ -763,6 +1143,7 @@ void compute_densities(ccsd_ctx* c, int k, int l) {
     ex.run(P.dens1);
   }
   sync(c);
+  if (c->opt.relax_orbitals) add_orbital_relaxation(c, k, l);
   c->dens_k = k;
   c->dens_l = l;
 }
@@ -822,7 +1203,7 @@ ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int
     c->opt = *opt;
   else
     ccsd_default_options(&c->opt);
-  if (c->opt.relax_orbitals) {
+  if (c->opt.relax_orbitals != 0 && c->opt.relax_orbitals != 1) {
     delete c;
     return CCSD_ERR_ARG;
   }
@@ -897,6 +1278,12 @@ ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int
       ex.set_precision(p0, c->opt.splits);
     }
     sync(c);
+    // orbital relaxation needs Hartree-Fock orbitals: F_ai = 0
+    if (c->opt.relax_orbitals) {
+      const double f = fock_ov_max(c);
+      if (!(f < 1e-8))
+        throw Err(CCSD_ERR_NOT_HF, "relax_orbitals needs Hartree-Fock orbitals: max |F_ia| = " + std::to_string(f));
+    }
   });
   if (s != CCSD_OK) {
     delete c;
@@ -1351,8 +1738,19 @@ long long ccsd_describe_program(const char* which, char* buf, size_t len) {
     else if (w == "hvp") p = &P.hvp;
     else if (w == "dens1") p = &P.dens1;
     else if (w == "dens0") p = &P.dens0;
+    HFPrograms H;
+    const Graph* g = &P.cp.g;
+    if (!p && w.rfind("hf_", 0) == 0) {
+      build_hf_programs(H);
+      g = &H.g;
+      if (w == "hf_fock") p = &H.fock;
+      else if (w == "hf_A") p = &H.hfA;
+      else if (w == "hf_rotT") p = &H.rotT;
+      else if (w == "hf_kdens") p = &H.kdens;
+      else if (w == "hf_rotate") p = &H.rotate;
+    }
     if (!p) return -1;
-    std::string s = dump(P.cp.g, *p);
+    std::string s = dump(*g, *p);
     if (buf && len > 0) {
       size_t m = std::min(len - 1, s.size());
       std::memcpy(buf, s.data(), m);
@@ -1653,13 +2051,7 @@ ccsd_status ccsd_batch_eom_solve(ccsd_batch b, int side, int nroots, double* ome
       std::vector<std::unique_ptr<DevBuf>> vecs;
       d[s]->results(vecs);
       d[s].reset();
-      if (refining(c)) {  // FP64 continuation of this system alone
-        PrecScope fp64(c, CCSD_PREC_FP64);
-        std::vector<std::unique_ptr<DevBuf>> fin;
-        const std::vector<double> wm = w;
-        its += davidson(c, side, nroots, w, fin, c->opt.tol_eom, &vecs, &wm);
-        vecs.swap(fin);
-      }
+      if (refining(c)) its += refine_roots(c, side, w, vecs);  // FP64 refinement of this system alone
       if (side == 0) {
         c->R.swap(vecs);
         finish_right(c, w);
@@ -1686,6 +2078,161 @@ void ccsd_batch_destroy(ccsd_batch b) {
   if (!b) return;
   batch_release(b);
   delete b;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Hartree-Fock orbitals for the relaxed mode
+// ---------------------------------------------------------------------------
+namespace {
+
+// exp(K) of an antisymmetric n x n matrix (host, row-major) into U (device):
+// scaling and squaring with a degree-16 Taylor polynomial (||K / 2^s||_1 <= 1/4,
+// truncation error below 1e-20 before squaring); the products run in the FP64 GEMM.
+void expm_device(const std::vector<double>& K, int n, double* U, cudaStream_t st) {
+  const int64_t nn = (int64_t)n * n;
+  double nrm = 0.0;
+  for (int q = 0; q < n; ++q) {
+    double col = 0.0;
+    for (int p = 0; p < n; ++p) col += std::fabs(K[(int64_t)p * n + q]);
+    nrm = std::max(nrm, col);
+  }
+  int s = 0;
+  while (std::ldexp(nrm, -s) > 0.25) ++s;
+  std::vector<double> Ks(nn), I(nn, 0.0);
+  for (int64_t e = 0; e < nn; ++e) Ks[e] = std::ldexp(K[e], -s);
+  for (int p = 0; p < n; ++p) I[(int64_t)p * n + p] = 1.0;
+  DevBuf X(nn), T(nn), T2(nn), S(nn);
+  CUDA_OK(cudaMemcpyAsync(X.p, Ks.data(), nn * sizeof(double), cudaMemcpyHostToDevice, st));
+  CUDA_OK(cudaMemcpyAsync(T.p, I.data(), nn * sizeof(double), cudaMemcpyHostToDevice, st));
+  CUDA_OK(cudaMemcpyAsync(S.p, I.data(), nn * sizeof(double), cudaMemcpyHostToDevice, st));
+  // C[m][q] = alpha sum_k A[m][k] Y[k][q]: the GEMM's second operand is read as [q][k]
+  auto mul = [&](const double* A, const double* Y, double* C, double alpha) {
+    GemmArgs g{};
+    g.batch = 1;
+    g.M = g.N = g.K = n;
+    g.A = A;
+    g.sAm = n;
+    g.sAk = 1;
+    g.B = Y;
+    g.sBn = 1;
+    g.sBk = n;
+    g.C = C;
+    g.sCm = n;
+    g.sCn = 1;
+    g.alpha = alpha;
+    g.beta = 0.0;
+    launch_dgemm(g, st);
+  };
+  for (int k = 1; k <= 16; ++k) {  // S = sum_k (K/2^s)^k / k!
+    mul(T.p, X.p, T2.p, 1.0 / k);
+    std::swap(T.p, T2.p);
+    launch_axpby(nn, 1.0, T.p, 1.0, S.p, st);
+  }
+  for (int q = 0; q < s; ++q) {
+    mul(S.p, S.p, T2.p, 1.0);
+    std::swap(S.p, T2.p);
+  }
+  CUDA_OK(cudaMemcpyAsync(U, S.p, nn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CUDA_OK(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+
+extern "C" {
+
+ccsd_status ccsd_scf(const double* eps, const double* h, const double* B, int o, int v, int naux, double tol,
+                     double* U_out, double* h_out, double* B_out, int* iters) {
+  if (!eps || !h || !B || !U_out || o < 1 || v < 1 || naux < 1 || !(tol > 0.0)) return CCSD_ERR_ARG;
+  return unguarded([&] {
+    const int n = o + v;
+    const int64_t nn = (int64_t)n * n, nz = (int64_t)naux * nn, m = (int64_t)o * v;
+    cudaStream_t st = nullptr;
+    DevBuf h0(nn), B0(nz), hr(nn), Br(nz), Ud(nn), f(m), ones(o);
+    CUDA_OK(cudaMemcpy(h0.p, h, nn * sizeof(double), cudaMemcpyDefault));
+    CUDA_OK(cudaMemcpy(B0.p, B, nz * sizeof(double), cudaMemcpyDefault));
+    std::vector<double> e(n), one(o, 1.0);
+    CUDA_OK(cudaMemcpy(e.data(), eps, n * sizeof(double), cudaMemcpyDefault));
+    CUDA_OK(cudaMemcpy(ones.p, one.data(), o * sizeof(double), cudaMemcpyHostToDevice));
+    HFPrograms P;
+    build_hf_programs(P);
+    Executor hx(P.g, o, v, naux, 1, st);
+    hx.set_precision(CCSD_PREC_FP64, 3);
+    hx.bind(P.ones_o, ones.p);
+    hx.bind(P.U, Ud.p);
+    hx.bind(P.hr, hr.p);
+    hx.bind(P.Br, Br.p);
+    hx.bind(P.F, f.p);
+    // Newton-type iterations on kappa: F'(exp(K(kappa)))_ia = 0, each step solving
+    // J(h', B') dkappa = -F' (J the local derivative dF'/dkappa, not symmetric away from
+    // the solution) at the current rotated integrals by GMRES
+    std::vector<double> kappa(m, 0.0), fh(m), K(nn);
+    int it = 0;
+    for (;; ++it) {
+      if (it > 100) throw Err(CCSD_ERR_NOT_CONVERGED, "Hartree-Fock equations not converged");
+      std::fill(K.begin(), K.end(), 0.0);
+      for (int i = 0; i < o; ++i)
+        for (int a = 0; a < v; ++a) {
+          K[(int64_t)(o + a) * n + i] = kappa[i * v + a];
+          K[(int64_t)i * n + o + a] = -kappa[i * v + a];
+        }
+      expm_device(K, n, Ud.p, st);
+      hx.bind(P.h, h0.p);
+      hx.bind(P.B, B0.p);
+      hx.run(P.rotate);
+      hx.bind(P.h, hr.p);
+      hx.bind(P.B, Br.p);
+      hx.run(P.fock);
+      CUDA_OK(cudaMemcpy(fh.data(), f.p, m * sizeof(double), cudaMemcpyDeviceToHost));
+      double fmax = 0.0;
+      for (double x : fh) fmax = std::max(fmax, std::fabs(x));
+      if (!std::isfinite(fmax)) throw Err(CCSD_ERR_NOT_CONVERGED, "Hartree-Fock iterations diverged");
+      if (fmax < tol) break;
+      std::vector<double> rhs(m);
+      for (int64_t q = 0; q < m; ++q) rhs[q] = -fh[q];
+      std::vector<double> dk = hf_solve_general(hx, P, o, v, st, rhs, e, 1e-4, 300);
+      for (int64_t q = 0; q < m; ++q) kappa[q] += dk[q];
+    }
+    CUDA_OK(cudaMemcpy(U_out, Ud.p, nn * sizeof(double), cudaMemcpyDefault));
+    if (h_out) CUDA_OK(cudaMemcpy(h_out, hr.p, nn * sizeof(double), cudaMemcpyDefault));
+    if (B_out) CUDA_OK(cudaMemcpy(B_out, Br.p, nz * sizeof(double), cudaMemcpyDefault));
+    if (iters) *iters = it;
+  });
+}
+
+ccsd_status ccsd_rotate_integrals(const double* U, const double* h, const double* B, int o, int v, int naux,
+                                  double* h_out, double* B_out) {
+  if (!U || !h || !B || !h_out || !B_out || o < 1 || v < 1 || naux < 1) return CCSD_ERR_ARG;
+  return unguarded([&] {
+    const int n = o + v;
+    const int64_t nn = (int64_t)n * n, nz = (int64_t)naux * nn;
+    DevBuf Ud(nn), hd(nn), Bd(nz), hr(nn), Br(nz);
+    CUDA_OK(cudaMemcpy(Ud.p, U, nn * sizeof(double), cudaMemcpyDefault));
+    CUDA_OK(cudaMemcpy(hd.p, h, nn * sizeof(double), cudaMemcpyDefault));
+    CUDA_OK(cudaMemcpy(Bd.p, B, nz * sizeof(double), cudaMemcpyDefault));
+    HFPrograms P;
+    build_hf_programs(P);
+    Executor hx(P.g, o, v, naux, 1, nullptr);
+    hx.set_precision(CCSD_PREC_FP64, 3);
+    hx.bind(P.h, hd.p);
+    hx.bind(P.B, Bd.p);
+    hx.bind(P.U, Ud.p);
+    hx.bind(P.hr, hr.p);
+    hx.bind(P.Br, Br.p);
+    hx.run(P.rotate);
+    CUDA_OK(cudaMemcpy(h_out, hr.p, nn * sizeof(double), cudaMemcpyDefault));
+    CUDA_OK(cudaMemcpy(B_out, Br.p, nz * sizeof(double), cudaMemcpyDefault));
+  });
+}
+
+ccsd_status ccsd_get_orbital_multipliers(ccsd_handle c, int k, int l, double* kbar) {
+  return guarded(c, [&] {
+    if (!c->opt.relax_orbitals) throw Err(CCSD_ERR_STATE, "the handle does not relax orbitals");
+    if (!kbar) throw Err(CCSD_ERR_ARG, "null output");
+    compute_densities(c, k, l);
+    CUDA_OK(cudaMemcpy(kbar, c->kbar.data(), c->kbar.size() * sizeof(double), cudaMemcpyDefault));
+  });
 }
 
 }  // extern "C"

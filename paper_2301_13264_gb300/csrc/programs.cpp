@@ -75,12 +75,13 @@ void build_programs(Programs& P) {
     P.dB = adj.at(cp.B);
     g.T[P.dH].role = g.T[P.dB].role = ROLE_OUTPUT;
   }
-  // densities with the ground right state: d/d(h,B) of z.Omega
+  // densities with the ground right state: d/d(h,B) of z.Omega + e E
   {
     std::set<int> need_h = dependents(g, cp.fwd, {cp.h, cp.B});
     P.eZ1 = g.add("eZ1", "ov", ROLE_SEED);
     P.eZ2 = g.add("eZ2", "oovv", ROLE_SEED);
-    std::map<int, int> adj = {{cp.O1, P.eZ1}, {cp.O2, P.eZ2}};
+    P.eE = g.add("eE", "", ROLE_SEED);
+    std::map<int, int> adj = {{cp.O1, P.eZ1}, {cp.O2, P.eZ2}, {cp.E, P.eE}};
     P.dens0 = vjp(g, cp.fwd, adj, need_h, false, "VE");
     P.eH = adj.at(cp.h);
     P.eB = adj.at(cp.B);

@@ -21,9 +21,9 @@ struct Programs {
   // densities: d/d(h,B) of z.Omega + g0 (eta.r) + g.(A r)  at fixed t
   Prog dens1;
   int dZ1, dZ2, dR1, dR2, dG1, dG2, dG0, dH, dB;
-  // densities of z.Omega alone (right ground state)
+  // densities of z.Omega + e E at fixed t (right ground state; e E adds the energy's own density)
   Prog dens0;
-  int eZ1, eZ2, eH, eB;
+  int eZ1, eZ2, eE, eH, eB;
 };
 
 void build_programs(Programs& P);

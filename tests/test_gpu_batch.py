@@ -131,7 +131,10 @@ def test_batch_errors():
                 B.ccsd_batch_transform(b, 0, xs, [x.copy() for x in xs])
             assert e.value.status == B.ERR_STATE
             with pytest.raises(B.CCSDError) as e:
-                B.ccsd_batch_eom_solve(b, 0, 3, len(hs))
+                B.ccsd_batch_eom_solve(b, 0, 3, len(hs))  # more roots than trial vectors per launch
+            assert e.value.status == B.ERR_ARG
+            with pytest.raises(B.CCSDError) as e:
+                B.ccsd_batch_eom_solve(b, 0, 2, len(hs))  # no ground state yet
             assert e.value.status == B.ERR_STATE
         finally:
             B.ccsd_batch_destroy(b)

@@ -56,7 +56,7 @@ def test_create_rejects_bad_arguments(L):
     with pytest.raises(binding.CCSDError) as e:
         binding.ccsd_create(H.eps, H.h, H.B, 0, 3, 4)
     assert e.value.status == binding.ERR_ARG
-    opt = binding.ccsd_default_options(relax_orbitals=1)
+    opt = binding.ccsd_default_options(relax_orbitals=2)  # 0 or 1 only
     with pytest.raises(binding.CCSDError) as e:
         binding.ccsd_create(H.eps, H.h, H.B, 2, 3, 4, opt)
     assert e.value.status == binding.ERR_ARG
@@ -122,7 +122,8 @@ def test_library_programs_match_oracle(programs, o, v, naux):
     x1, x2, xe = cc.hamiltonian_derivative_jacobian(T(t1), T(t2), T(r1), T(r2), h, B, T(H.h1), T(H.B1), o)
     ref = float(cc.pdot(T(z1), T(z2), ox1, ox2) + 0.7 * xe + cc.pdot(T(g1), T(g2), x1, x2))
     assert abs(F - ref) < 1e-13 * max(1.0, abs(ref))
-    I.arr.update(eZ1=z1, eZ2=w * z2)
+    I.arr.update(eZ1=z1, eZ2=w * z2, eE=np.array(0.3))
     I.run(programs["dens0"])
     F = (I.arr["VE(h)"] * H.h1).sum() + (I.arr["VE(B)"] * H.B1).sum()
-    assert abs(F - float(cc.pdot(T(z1), T(z2), ox1, ox2))) < 1e-13
+    _, _, ex = cc.hamiltonian_derivative_residual(T(t1), T(t2), h, B, T(H.h1), T(H.B1), o)
+    assert abs(F - float(cc.pdot(T(z1), T(z2), ox1, ox2)) - 0.3 * float(ex)) < 1e-13
