@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of the single-system bench, time batched transforms of this many small systems")
     ap.add_argument("--no-autotune", action="store_true", help="batch mode: tile widths from the output width")
+    ap.add_argument("--mlp", action="store_true", help="instead, time the learned-guess kernels at the workload size")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -475,8 +476,61 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def run_mlp(args):
+    """Learned-guess kernels at a workload's size: features of every doubles element,
+    inference over all of them (tensor-core kernel), and training steps."""
+    import torch
+    from paper_2301_13264_gb300 import binding as B
+    from paper_2301_13264_gb300.synth import workload
+
+    H = workload(args.workload)
+    o, v = H.o, H.v
+    n2 = o * o * v * v
+    h = B.ccsd_create(H.eps, H.h, H.B, o, v, H.naux, B.ccsd_default_options(precision=B.PREC_MIXED))
+    X = torch.zeros((n2, 3), dtype=torch.float32, device="cuda")
+    out = torch.zeros(n2, dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(0)
+    model = np.zeros(B.MLP_PARAMS, dtype=np.float32)
+    model[:B.MLP_TRAINABLE] = rng.normal(0.0, 0.1, B.MLP_TRAINABLE)
+    model[B.MLP_TRAINABLE + 3:B.MLP_TRAINABLE + 6] = 1.0
+    model[B.MLP_TRAINABLE + 6] = 1.0
+    m_dev = torch.as_tensor(model, device="cuda")
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    f_ms = timed(lambda: B.ccsd_guess_features(h, X), args.steps)
+    p_ms = timed(lambda: B.ccsd_mlp_predict(m_dev, X, out), args.steps)
+    T = torch.zeros(min(n2, 4_000_000), dtype=torch.float32, device="cuda")
+    Xs = X[:T.shape[0]].contiguous()
+    t0 = time.perf_counter()
+    B.ccsd_mlp_train(Xs, T, 200, 8192, 1e-3, 1)
+    torch.cuda.synchronize()
+    tr_s = time.perf_counter() - t0
+    B.ccsd_destroy(h)
+    flop_row = 2 * (3 * 128 + 128 * 128 + 128)
+    peaks, src = load_peaks()
+    print(json.dumps({"metric": "learned-guess kernels", "workload": f"{args.workload} o={o} v={v}", "rows": n2,
+                      "features_ms": f_ms, "inference_ms": p_ms, "inference_rows_per_s": n2 / (p_ms * 1e-3),
+                      "inference_tflops": n2 * flop_row / (p_ms * 1e-3) / 1e12,
+                      "inference_frac_of_bf16_peak": n2 * flop_row / (p_ms * 1e-3) / 1e12 / peaks["bf16_tflops"],
+                      "train_200_steps_s": tr_s, "train_rows_per_s": 200 * 8192 / tr_s,
+                      "peak_source": f"bf16_tflops of {src} MEASURED_PEAKS.json"}), flush=True)
+
+
 def main():
     args = parse()
+    if args.mlp:
+        run_mlp(args)
+        return
     if args.ttc:
         run_ttc(args)
         return

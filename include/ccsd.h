@@ -26,7 +26,9 @@
  * - Streams: all GPU work runs on options.stream (0 = the legacy default
  *   stream).  Calls that return host values synchronise that stream.
  * - Errors: every call returns a ccsd_status; no C++ exception crosses the
- *   ABI.  ccsd_last_error(handle) gives the message of the last failure.
+ *   ABI.  ccsd_last_error(handle) gives the message of the last failure;
+ *   ccsd_last_error(NULL) that of the calling thread's last failed call made
+ *   without a handle (ccsd_scf, ccsd_mlp_*, ...).
  * - Threads: a handle must not be used by two threads at once.
  * - State indices: k, l in {0 = ground state, 1..nroots}; the excited states
  *   are those of the last eom_solve_right/left pair.  For k = 0 the left

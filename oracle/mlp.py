@@ -73,6 +73,26 @@ def forward(model, X):
     return (h2 @ w3 + b3) * tscale
 
 
+def forward_inference(model, X):
+    """Predictions of the inference arithmetic: every weight rounded to bf16, the first
+    hidden layer's output rounded to bf16 (it is the operand of the second layer's
+    bf16 product), everything else in FP64."""
+    W1, b1, W2, b2, w3, b3, mean, scale, tscale = unpack(bf16_weights(model))
+    xn = (np.asarray(X, dtype=np.float32).astype(np.float64) - mean) / scale
+    h1 = round_bf16(np.tanh(xn @ W1.T + b1).astype(np.float32))
+    h2 = np.tanh(h1 @ W2.T + b2)
+    return (h2 @ w3 + b3) * tscale
+
+
+def inference_flip_bound(model):
+    """Largest change of one prediction when a single first-layer activation moves by
+    one bf16 unit in the last place (2^-8 relative, |h1| <= 1): the inference kernel
+    and forward_inference may round an activation that sits within FP32 rounding of
+    a bf16 tie differently."""
+    W1, b1, W2, b2, w3, b3, mean, scale, tscale = unpack(bf16_weights(model))
+    return 2.0 ** -8 * float(np.max(np.sum(np.abs(w3)[:, None] * np.abs(W2), axis=0))) * abs(tscale)
+
+
 def loss_and_grad(model, X, T):
     """(L, dL/dw[N_TRAIN]) for L = mean_r (y_r - T_r / tscale)^2, by reverse-mode chain rule."""
     W1, b1, W2, b2, w3, b3, mean, scale, tscale = unpack(model)

@@ -132,7 +132,8 @@ def _ptr(x):
 
 def _check(h, status):
     if status != OK:
-        msg = lib().ccsd_last_error(h).decode() if h else lib().ccsd_strerror(status).decode()
+        msg = lib().ccsd_last_error(h).decode() if h else (lib().ccsd_strerror(status).decode() + ": " +
+                                                         lib().ccsd_last_error(None).decode())
         raise CCSDError(status, msg)
 
 

@@ -35,6 +35,9 @@ struct Err : std::runtime_error {
   Err(ccsd_status c, const std::string& m) : std::runtime_error(m), code(c) {}
 };
 
+// message of the last failed call made without a handle (per thread)
+thread_local std::string g_last_error;
+
 #define CUDA_OK(x)                                                                                 \
   do {                                                                                             \
     cudaError_t e_ = (x);                                                                          \
@@ -606,6 +609,15 @@ int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std:
 
 int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol);
 
+// CCSD_VERBOSE=1: solver progress on stderr
+bool verbose_solvers() {
+  static const bool v = [] {
+    const char* e = getenv("CCSD_VERBOSE");
+    return e && e[0] == '1';
+  }();
+  return v;
+}
+
 // FP64 refinement of mixed-precision eigenpairs (w, vecs) to tol_eom: defect
 // correction root by root, falling back to an FP64 Davidson continuation that
 // follows the same roots if a correction stalls.  Returns the transforms used.
@@ -657,7 +669,7 @@ int davidson_refined(ccsd_ctx* c, int side, int nroots, std::vector<double>& w,
 // residual tolerance: per outer step one FP64 transform gives r = A x - w x (w the
 // Rayleigh quotient of the unit vector x); the correction d (d perpendicular to x)
 // solves the projected equation P (A - w) P d = -r, P = 1 - x x^T, by preconditioned
-// Jacobi + DIIS with transforms at the handle's (mixed) precision, to 1e-3 of |r|;
+// Jacobi + DIIS with transforms at the handle's (mixed) precision, to 1e-4 of |r|;
 // x += d.  Each step gains the mixed operator's accuracy (~5 digits), so two or three
 // FP64 transforms per root replace an FP64 Davidson continuation.  Returns the number
 // of transforms (FP64 + mixed); throws if the residual stops decreasing.
@@ -688,6 +700,8 @@ int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol) {
     launch_axpby(dim, 1.0, ax.p, 0.0, r.p, c->st);
     launch_axpby(dim, -w, x, 1.0, r.p, c->st);
     const double rn = std::sqrt(std::max(gram(c, r.p, dim, 1, r.p, dim, 1)[0], 0.0));
+    if (verbose_solvers())
+      fprintf(stderr, "[refine side %d] outer %d: w = %.12f, |r| = %.3e (%d transforms so far)\n", side, outer, w, rn, n);
     if (rn < tol) return n;
     if (!(rn < 0.5 * last)) throw Err(CCSD_ERR_NOT_CONVERGED, "eigenpair refinement stalled");
     last = rn;
@@ -696,7 +710,7 @@ int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol) {
     launch_axpby(dim, 0.0, d.p, -1.0, d.p, c->st);
     project(d.p);
     Diis diis(c, c->opt.diis_dim);
-    for (int it = 0; it < 40; ++it) {
+    for (int it = 0; it < 60; ++it) {
       transform(d.p, ad.p);
       ++n;
       launch_axpby(dim, 1.0, ad.p, 0.0, res.p, c->st);
@@ -704,7 +718,8 @@ int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol) {
       project(res.p);
       launch_axpby(dim, 1.0, r.p, 1.0, res.p, c->st);
       const double en = std::sqrt(std::max(gram(c, res.p, dim, 1, res.p, dim, 1)[0], 0.0));
-      if (en < 1e-3 * rn) break;
+      if (verbose_solvers()) fprintf(stderr, "[refine side %d]   inner %d: |res| = %.3e\n", side, it, en);
+      if (en < 1e-4 * rn || en < 0.1 * tol) break;
       launch_precond(c->vs, c->eps.p, res.p, dn.p, w, c->st);
       launch_axpby(dim, 1.0, d.p, -1.0, dn.p, c->st);  // dn = d - res / (D - w)
       project(dn.p);
@@ -1190,7 +1205,10 @@ const char* ccsd_strerror(ccsd_status s) {
   return "unknown status";
 }
 
-const char* ccsd_last_error(ccsd_handle h) { return h ? h->err.c_str() : "null handle"; }
+const char* ccsd_last_error(ccsd_handle h) {
+  if (h) return h->err.c_str();
+  return g_last_error.empty() ? "no error recorded" : g_last_error.c_str();
+}
 
 ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int o, int v, int naux,
                         const ccsd_options* opt, ccsd_handle* out) {
@@ -1579,11 +1597,14 @@ ccsd_status unguarded(F&& f) {
     f();
     return CCSD_OK;
   } catch (const Err& e) {
+    g_last_error = e.what();
     return e.code;
   } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
     return CCSD_ERR_OOM;
   } catch (const std::exception& e) {
-    return std::string(e.what()).find("out of memory") != std::string::npos ? CCSD_ERR_OOM : CCSD_ERR_CUDA;
+    g_last_error = e.what();
+    return g_last_error.find("out of memory") != std::string::npos ? CCSD_ERR_OOM : CCSD_ERR_CUDA;
   }
 }
 
@@ -1648,11 +1669,27 @@ ccsd_status ccsd_mlp_train(const float* X, const float* T, long long n, int step
 ccsd_status ccsd_mlp_predict(const float* model, const float* X, long long n, float* out) {
   if (!model || !X || !out || n < 1) return CCSD_ERR_ARG;
   return unguarded([&] {
-    DevBuf dM, dX, dO((n + 1) / 2);
-    floats_to_device(model, mlp::kParams, dM);
-    floats_to_device(X, n * 3, dX);
-    mlp::predict((const float*)dM.p, (const float*)dX.p, n, (float*)dO.p, 0);
-    CUDA_OK(cudaMemcpy(out, dO.p, n * sizeof(float), cudaMemcpyDefault));
+    // device arrays are used in place; host arrays are staged
+    DevBuf dM, dX, dO;
+    const float* m = model;
+    const float* x = X;
+    float* o = out;
+    if (!is_device_ptr(model)) {
+      floats_to_device(model, mlp::kParams, dM);
+      m = (const float*)dM.p;
+    }
+    if (!is_device_ptr(X)) {
+      floats_to_device(X, n * 3, dX);
+      x = (const float*)dX.p;
+    }
+    const bool odev = is_device_ptr(out);
+    if (!odev) {
+      dO.alloc((n + 1) / 2);
+      o = (float*)dO.p;
+    }
+    mlp::predict(m, x, n, o, 0);
+    if (!odev) CUDA_OK(cudaMemcpy(out, dO.p, n * sizeof(float), cudaMemcpyDefault));
+    CUDA_OK(cudaDeviceSynchronize());
   });
 }
 
@@ -1675,10 +1712,14 @@ ccsd_status ccsd_guess_features(ccsd_handle c, float* X) {
   return guarded(c, [&] {
     if (!X) throw Err(CCSD_ERR_ARG, "null output");
     const int64_t n2 = c->dim - c->n1;
-    DevBuf dX((n2 * 3 + 1) / 2);
     const double* gov = c->ex->ptr(c->P.cp.g.id("Govov"));
-    mlp::features(gov, c->eps.p, c->o, c->v, (float*)dX.p, c->st);
-    CUDA_OK(cudaMemcpyAsync(X, dX.p, n2 * 3 * sizeof(float), cudaMemcpyDefault, c->st));
+    if (is_device_ptr(X)) {
+      mlp::features(gov, c->eps.p, c->o, c->v, X, c->st);
+    } else {
+      DevBuf dX((n2 * 3 + 1) / 2);
+      mlp::features(gov, c->eps.p, c->o, c->v, (float*)dX.p, c->st);
+      CUDA_OK(cudaMemcpyAsync(X, dX.p, n2 * 3 * sizeof(float), cudaMemcpyDefault, c->st));
+    }
     sync(c);
   });
 }
@@ -2183,6 +2224,7 @@ ccsd_status ccsd_scf(const double* eps, const double* h, const double* B, int o,
       hx.run(P.rotate);
       hx.bind(P.h, hr.p);
       hx.bind(P.B, Br.p);
+      hx.bind(P.F, f.p);
       hx.run(P.fock);
       CUDA_OK(cudaMemcpy(fh.data(), f.p, m * sizeof(double), cudaMemcpyDeviceToHost));
       double fmax = 0.0;

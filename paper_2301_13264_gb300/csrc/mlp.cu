@@ -18,8 +18,10 @@
 #include <stdexcept>
 #include <vector>
 
+#include "exec.h"
 #include "kernels.cuh"
 #include "mlp.h"
+#include "tcgen05.cuh"
 
 namespace ccsd {
 namespace mlp {
@@ -186,6 +188,135 @@ __global__ void k_sample(int64_t* idx, int batch, int64_t n, unsigned long long 
   idx[i] = (int64_t)(z % (unsigned long long)n);
 }
 
+// ---------------------------------------------------------------------------
+// Inference on the tensor cores.  One CTA of 128 threads owns a 128-row tile at a
+// time (persistent over tiles): thread t computes row t's first layer in FP32,
+// rounds h1 to bf16 and writes it into the A operand in the 128-byte-swizzled
+// K-major layout a TMA copy would produce (two 64-wide K chunks); W2 sits in the
+// same layout as the B operand for the CTA's life.  One elected thread issues the
+// 128 x 128 x 128 product as 8 tcgen05.mma (kind::f16, FP32 accumulate in TMEM);
+// after the commit barrier each warp reads its 32 TMEM lanes (= rows) and applies
+// tanh, w3 and b3 in registers.  Waits are bounded; on timeout the kernel raises
+// the error flag and leaves.
+// ---------------------------------------------------------------------------
+constexpr int TILE_BYTES = 128 * 64 * 2;  // one 128-row x 64-column bf16 chunk
+
+// byte offset of element (row, k) (k < 64) in a 128B-swizzled chunk
+__device__ __forceinline__ uint32_t swz(int row, int k) {
+  return (uint32_t)(row * 128 + ((((k >> 3) ^ row) & 7) << 4) + ((k & 7) << 1));
+}
+
+__global__ void __launch_bounds__(H, 2)
+    k_mlp_infer_tc(const float* __restrict__ model, const float* __restrict__ X, int64_t n, float* __restrict__ out,
+                   int* err) {
+  extern __shared__ uint8_t raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = sm;                  // 2 chunks: h1 [128 rows][128 k]
+  uint8_t* sB = sm + 2 * TILE_BYTES;  // 2 chunks: W2 [128 out][128 in]
+  float* par = (float*)(sm + 4 * TILE_BYTES);  // W1[128][3], b1, b2, w3 (bf16-rounded)
+  float* sW1 = par;
+  float* sb1 = par + 3 * H;
+  float* sb2 = sb1 + H;
+  float* sw3 = sb2 + H;
+  uint64_t* bar = (uint64_t*)(sw3 + H);
+  uint32_t* tslot = (uint32_t*)(bar + 1);
+  const int t = threadIdx.x, warp = t >> 5;
+  if (*(volatile int*)err) return;
+  for (int e = t; e < H * H; e += H) {
+    const int j = e / H, k = e % H;
+    *(__nv_bfloat16*)(sB + (k >> 6) * TILE_BYTES + swz(j, k & 63)) = __float2bfloat16(model[OW2 + e]);
+  }
+  for (int e = t; e < 3 * H; e += H) sW1[e] = round_bf16(model[OW1 + e]);
+  sb1[t] = round_bf16(model[OB1 + t]);
+  sb2[t] = round_bf16(model[OB2 + t]);
+  sw3[t] = round_bf16(model[OW3 + t]);
+  const float b3 = round_bf16(model[OB3]);
+  float mean[3], scale[3];
+  for (int d = 0; d < 3; ++d) {
+    mean[d] = model[OMEAN + d];
+    scale[d] = model[OSCALE + d];
+  }
+  const float tscale = model[OTSCALE];
+  const uint32_t mbar = tc::smem_u32(bar);
+  if (t == 0) {
+    tc::mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(tslot)),
+                 "r"(H)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  const int64_t ntiles = (n + H - 1) / H;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const int64_t row = tile * H + t;
+    float x[3] = {0.f, 0.f, 0.f};
+    if (row < n)
+      for (int d = 0; d < 3; ++d) x[d] = (X[row * 3 + d] - mean[d]) / scale[d];
+    // first layer -> bf16 A operand, 8 units (one 16-byte chunk) at a time
+    for (int k0 = 0; k0 < H; k0 += 8) {
+      uint32_t pk[4];
+      for (int q = 0; q < 4; ++q) {
+        const int k = k0 + 2 * q;
+        const float h0 = tanhf(sW1[k * 3] * x[0] + sW1[k * 3 + 1] * x[1] + sW1[k * 3 + 2] * x[2] + sb1[k]);
+        const float h1 =
+            tanhf(sW1[(k + 1) * 3] * x[0] + sW1[(k + 1) * 3 + 1] * x[1] + sW1[(k + 1) * 3 + 2] * x[2] + sb1[k + 1]);
+        __nv_bfloat162 v = __floats2bfloat162_rn(h0, h1);
+        pk[q] = *reinterpret_cast<uint32_t*>(&v);
+      }
+      *reinterpret_cast<uint4*>(sA + (k0 >> 6) * TILE_BYTES + swz(t, k0 & 63)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc::fence_before();
+    __syncthreads();
+    if (t == 0) {
+      tc::fence_after();
+      for (int kc = 0; kc < 2; ++kc)
+        for (int j = 0; j < 4; ++j)
+          tc::mma_bf16(tmem, tc::smem_desc(tc::smem_u32(sA + kc * TILE_BYTES) + 32 * j),
+                       tc::smem_desc(tc::smem_u32(sB + kc * TILE_BYTES) + 32 * j), tc::idesc<H>(),
+                       (kc | j) != 0 ? 1u : 0u);
+      tc::mma_commit(mbar);
+    }
+    __syncwarp();
+    ok = tc::mbar_wait(mbar, phase, err);
+    phase ^= 1u;
+    tc::fence_after();
+    if (!ok) {
+      atomicExch(err, 1);
+      // the product may still be running: give it a bounded second wait before TMEM is freed
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait(mbar, phase ^ 1u) && clock64() - t0 < tc::TIMEOUT_CYCLES) {
+      }
+      break;
+    }
+    float y = b3;
+    for (int c = 0; c < H; c += 32) {
+      uint32_t r[32];
+      tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) y += sw3[c + j] * tanhf(__uint_as_float(r[j]) + sb2[c + j]);
+    }
+    if (row < n) out[row] = y * tscale;
+    tc::fence_before();
+    __syncthreads();  // A tile and accumulator are reused by the next tile
+    tc::fence_after();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(H) : "memory");
+}
+
+constexpr size_t kInferSmem = 1024 + 4 * TILE_BYTES + 6 * H * sizeof(float) + 64;
+
 size_t smem_bytes(int mode) { return sizeof(float) * ((mode ? 2 : 1) * H * P2 + 3 * TR * H + TR * 4 + TR + TR * 4); }
 
 static int grid_for_rows(int64_t n) {
@@ -193,14 +324,27 @@ static int grid_for_rows(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(t, 152 * 4));
 }
 
+__device__ int g_mlp_err = 0;
+
 void predict(const float* model, const float* X, int64_t n, float* out, cudaStream_t st) {
   static bool attr = false;
+  static int* err = nullptr;
   if (!attr) {
-    cudaFuncSetAttribute(k_mlp<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(0));
+    cudaFuncSetAttribute(k_mlp_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInferSmem);
+    cudaGetSymbolAddress((void**)&err, g_mlp_err);
     attr = true;
   }
+  const int64_t tiles = (n + H - 1) / H;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 152 * 2));
   count_launches(1);
-  k_mlp<0><<<grid_for_rows(n), H, smem_bytes(0), st>>>(model, X, nullptr, nullptr, n, 0.f, out, nullptr, nullptr);
+  k_mlp_infer_tc<<<grid, H, kInferSmem, st>>>(model, X, n, out, err);
+  int h = 0;
+  cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  if (h) {
+    cudaMemsetAsync(err, 0, sizeof(int), st);
+    throw DeviceTimeout("a tensor-core wait in the MLP inference kernel exceeded its budget");
+  }
 }
 
 void gradient(const float* model, const float* X, const float* T, const int64_t* idx, int64_t n, float* grad,

@@ -52,9 +52,14 @@ def test_predict_matches_oracle_with_bf16_weights(n):
     X = rng.normal(0.0, 1.5, (n, 3)).astype(np.float32)
     out = np.zeros(n, dtype=np.float32)
     b.ccsd_mlp_predict(m, X, out)
-    ref = omlp.forward(omlp.bf16_weights(m), X)
-    # FP32 arithmetic on identical bf16 weights: differences of rounding order only
-    assert np.abs(out - ref).max() <= 2e-5 * np.abs(ref).max()
+    ref = omlp.forward_inference(m, X)
+    # bf16 weights and bf16 first-layer activations on both sides; FP32 accumulation and
+    # FP32 tanh in the kernel.  An activation within FP32 rounding of a bf16 tie may round
+    # the other way (about 2^-15 of them): allow a few such flips per row, plus FP32 noise.
+    err = np.abs(out - ref)
+    assert err.max() <= 3 * omlp.inference_flip_bound(m) + 2e-5 * np.abs(ref).max(), err.max()
+    # almost every row agrees to FP32 accumulation accuracy
+    assert np.quantile(err, 0.99) <= 2e-5 * np.abs(ref).max()
 
 
 def test_features_match_oracle():

@@ -127,3 +127,46 @@ def test_library_programs_match_oracle(programs, o, v, naux):
     F = (I.arr["VE(h)"] * H.h1).sum() + (I.arr["VE(B)"] * H.B1).sum()
     _, _, ex = cc.hamiltonian_derivative_residual(T(t1), T(t2), h, B, T(H.h1), T(H.B1), o)
     assert abs(F - float(cc.pdot(T(z1), T(z2), ox1, ox2)) - 0.3 * float(ex)) < 1e-13
+
+
+@pytest.mark.parametrize("o,v,naux", [(2, 4, 6), (3, 5, 9)])
+def test_orbital_programs_match_oracle(L, o, v, naux):
+    """The library's Hartree-Fock programs (Fock ov block, A^HF x, the adjoint of the
+    rotation map, the kappa-bar densities, the integral rotation) executed by the
+    interpreter against the oracle's definitions."""
+    from oracle import relaxed as rx
+    H = make_hamiltonian(o, v, naux, seed=5)
+    rng = np.random.default_rng(9)
+    n = o + v
+    base = dict(h=H.h.copy(), B=H.B.copy(), ones_o=np.ones(o))
+
+    def run(which, **arrs):
+        I = Interp(o, v, naux)
+        I.arr.update(base)
+        I.arr.update(arrs)
+        I.run(binding.ccsd_describe_program(which))
+        return I.arr
+
+    F = rx.fock(H.h, H.B, o)[:o, o:].numpy()
+    assert np.abs(run("hf_fock")["Fov"] - F).max() < 1e-13
+    x = rng.normal(size=(o, v))
+    A = rx.hf_hessian(H.h, H.B, o).numpy()
+    assert np.abs(run("hf_A", kx=x)["HA(Fov)"] - (A @ x.reshape(-1)).reshape(o, v)).max() < 1e-12
+    # adjoint of the rotation map: <x-bar, x> = <D, dh(x)> + <Z, dB(x)>
+    D, Z = rng.normal(size=(n, n)), rng.normal(size=(naux, n, n))
+    xbar = run("hf_rotT", rotT_D=D, rotT_Z=Z)["RT(kx)"]
+    K = rx.kappa_matrix(x, o, n).numpy()
+    dh = K.T @ H.h + H.h @ K
+    dB = np.einsum("rp,Jrq->Jpq", K, H.B) + np.einsum("Jpr,rq->Jpq", H.B, K)
+    assert abs((xbar * x).sum() - (D * dh).sum() - (Z * dB).sum()) < 1e-11
+    # kappa-bar densities: <kH, h1> + <kB, B1> = kbar . dF_ov along (h1, B1)
+    kb = rng.normal(size=(o, v))
+    out = run("hf_kdens", kbar=kb)
+    _, dF = torch.func.jvp(lambda hh, BB: rx.fock(hh, BB, o)[:o, o:], (cc.as_t(H.h), cc.as_t(H.B)),
+                           (cc.as_t(H.h1), cc.as_t(H.B1)))
+    lhs = (out["KD(h)"] * H.h1).sum() + (out["KD(B)"] * H.B1).sum()
+    assert abs(lhs - float((cc.as_t(kb) * dF).sum())) < 1e-12
+    U = torch.linalg.matrix_exp(rx.kappa_matrix(x * 0.1, o, n)).numpy()
+    out = run("hf_rotate", U=U)
+    hr, Br = rx.rotate(H.h, H.B, U)
+    assert np.abs(out["h_rot"] - hr.numpy()).max() < 1e-13 and np.abs(out["B_rot"] - Br.numpy()).max() < 1e-13

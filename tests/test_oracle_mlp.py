@@ -108,3 +108,17 @@ def test_features_from_zero_amplitude_residual():
                     assert X[i, j, a, b, 1] == pytest.approx(D, rel=1e-14)
                     assert X[i, j, a, b, 0] == pytest.approx(-g[i, j, a, b] / D, rel=1e-10, abs=1e-14)
                     assert X[i, j, a, b, 2] == pytest.approx(abs(g[i, j, a, b]), rel=1e-10, abs=1e-14)
+
+
+def test_inference_arithmetic_within_rounding_bound():
+    # bf16 rounding of every first-layer activation (|h1| <= 1, error <= 2^-9 each)
+    # moves a prediction by at most 2^-9 sum_jk |w3_j W2_jk| tscale
+    rng = np.random.default_rng(8)
+    m = _random_model(rng, 0.2)
+    X = rng.normal(0.0, 1.0, (300, 3)).astype(np.float32)
+    a = mlp.forward_inference(m, X)
+    b = mlp.forward(mlp.bf16_weights(m), X)
+    W1, b1, W2, b2, w3, b3, mean, scale, tscale = mlp.unpack(mlp.bf16_weights(m))
+    bound = 2.0 ** -9 * float(np.sum(np.abs(w3)[:, None] * np.abs(W2))) * abs(tscale)
+    assert np.abs(a - b).max() <= bound
+    assert np.abs(a - b).max() > 0  # the rounding is really applied
