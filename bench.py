@@ -52,9 +52,27 @@ def parse():
                     help="instead of the single-system bench, time batched transforms of this many small systems")
     ap.add_argument("--no-autotune", action="store_true", help="batch mode: tile widths from the output width")
     ap.add_argument("--mlp", action="store_true", help="instead, time the learned-guess kernels at the workload size")
+    ap.add_argument("--batch-eom", type=int, default=0,
+                    help="with --batch: time the batched right EOM solve for this many roots instead")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
+
+
+def allreduce_max(value, world, device):
+    """The largest of the ranks' values (the slowest rank's time); the value itself at N = 1."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
 
 
 def load_peaks():
@@ -254,12 +272,9 @@ def run_ours(args, rank, world, local_rank):
     prof = B.ccsd_profile_stop(h)
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = allreduce_max(ms, world, "cuda")
+    value = job_throughput(2 * args.nvec * args.steps, world, ms / 1e3)
     n_tr = 2 * args.nvec * args.steps * world
-    value = n_tr / (ms / 1e3)
 
     # separate right/left rates (short extra runs, not part of the timed region)
     def timed(side, reps=2):
@@ -288,10 +303,7 @@ def run_ours(args, rank, world, local_rank):
             B.ccsd_jacobian_transform(h, 1, args.nvec, Xh, Yh)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([el], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            el = float(tt.item())
+        el = allreduce_max(el, world, "cuda")
         nbytes = 2 * args.nvec * dim * 8
         e2e = {"value": n_tr / el, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
 
@@ -476,6 +488,51 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batch_eom(args):
+    """Right EOM roots of many small systems: the lockstep batched Davidson (one graph
+    launch per iteration for all systems) against per-system solves, same handles and
+    thresholds."""
+    import torch
+    from paper_2301_13264_gb300 import binding as B
+    from paper_2301_13264_gb300.synth import make_hamiltonian
+
+    shapes = batch_shapes(args.batch)
+    nroots = args.batch_eom
+    prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_FP64
+    hs = []
+    t0 = time.perf_counter()
+    for k, (o, v, naux) in enumerate(shapes):
+        H = make_hamiltonian(o, v, naux, seed=500 + k)
+        opt = B.ccsd_default_options(precision=prec, splits=args.splits, autotune=int(not args.no_autotune),
+                                     tol_res=1e-8, tol_eom=1e-6, tol_lin=1e-8, refine=1, max_iter=200)
+        h = B.ccsd_create(H.eps, H.h, H.B, o, v, naux, opt)
+        B.ccsd_solve_ground(h)
+        hs.append(h)
+    setup = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    w_seq = [B.eom_solve_right(h, nroots)[0] for h in hs]
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    b = B.ccsd_batch_create(hs, args.nvec)
+    t0 = time.perf_counter()
+    w_bat, iters = B.ccsd_batch_eom_solve(b, 0, nroots, len(hs))
+    torch.cuda.synchronize()
+    bat_s = time.perf_counter() - t0
+    st = B.ccsd_batch_stats(b)
+    B.ccsd_batch_destroy(b)
+    for h in hs:
+        B.ccsd_destroy(h)
+    diff = float(np.abs(np.array(w_seq) - w_bat).max())
+    print(json.dumps({"metric": "batched EOM solve", "unit": "s", "higher_is_better": False,
+                      "config": {"workload": f"{len(hs)} systems, o~U{{4..20}}, v~U{{30..120}}, naux=3.5(o+v)",
+                                 "nroots": nroots, "nvec": args.nvec, "precision": args.precision,
+                                 "tol_eom": 1e-6, "refine": 1},
+                      "sequential_s": seq_s, "batched_s": bat_s, "speedup": seq_s / bat_s,
+                      "max_root_diff": diff, "max_iterations": max(iters), "graph": st, "setup_s": setup}),
+          flush=True)
+
+
 def run_mlp(args):
     """Learned-guess kernels at a workload's size: features of every doubles element,
     inference over all of them (tensor-core kernel), and training steps."""
@@ -533,6 +590,9 @@ def main():
         return
     if args.ttc:
         run_ttc(args)
+        return
+    if args.batch and args.batch_eom:
+        run_batch_eom(args)
         return
     if args.batch:
         run_batch(args)

@@ -607,7 +607,8 @@ int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std:
   return d.iterations;
 }
 
-int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol);
+int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol,
+                     const std::vector<const double*>& others);
 
 // CCSD_VERBOSE=1: solver progress on stderr
 bool verbose_solvers() {
@@ -625,7 +626,12 @@ int refine_roots(ccsd_ctx* c, int side, std::vector<double>& w, std::vector<std:
   const int nroots = (int)w.size();
   int n = 0;
   try {
-    for (int k = 0; k < nroots; ++k) n += refine_eigenpair(c, side, vecs[k]->p, w[k], c->opt.tol_eom);
+    for (int k = 0; k < nroots; ++k) {
+      std::vector<const double*> others;
+      for (int j = 0; j < nroots; ++j)
+        if (j != k) others.push_back(vecs[j]->p);
+      n += refine_eigenpair(c, side, vecs[k]->p, w[k], c->opt.tol_eom, others);
+    }
     return n;
   } catch (const Err& e) {
     if (e.code != CCSD_ERR_NOT_CONVERGED) throw;
@@ -667,30 +673,52 @@ int davidson_refined(ccsd_ctx* c, int side, int nroots, std::vector<double>& w,
 
 // Defect correction of one eigenpair (x, w) of A (side 0) or A^T (side 1) to the FP64
 // residual tolerance: per outer step one FP64 transform gives r = A x - w x (w the
-// Rayleigh quotient of the unit vector x); the correction d (d perpendicular to x)
-// solves the projected equation P (A - w) P d = -r, P = 1 - x x^T, by preconditioned
-// Jacobi + DIIS with transforms at the handle's (mixed) precision, to 1e-4 of |r|;
+// Rayleigh quotient of the unit vector x); the correction d solves the projected
+// equation P (A - w) P d = -P r, P = 1 - Q Q^T with Q an orthonormal basis of x and
+// the other roots' vectors (deflation), by preconditioned Jacobi + DIIS with
+// transforms at the handle's (mixed) precision, to 1e-4 of |P r|;
 // x += d.  Each step gains the mixed operator's accuracy (~5 digits), so two or three
 // FP64 transforms per root replace an FP64 Davidson continuation.  Returns the number
 // of transforms (FP64 + mixed); throws if the residual stops decreasing.
-int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol) {
+int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol,
+                     const std::vector<const double*>& others) {
   const int64_t dim = c->dim;
-  DevBuf ax(dim), r(dim), d(dim), ad(dim), res(dim), dn(dim);
+  const int nq = 1 + (int)others.size();
+  DevBuf ax(dim), r(dim), d(dim), ad(dim), res(dim), dn(dim), Q(nq * dim);
   auto transform = [&](const double* in, double* out) {
     if (side == 0)
       right_block(c, in, out, 1);
     else
       left_block(c, in, out, 1);
   };
-  auto project = [&](double* v) {  // v -= x <x|v>
-    const double s = gram(c, x, dim, 1, v, dim, 1)[0];
-    launch_axpby(dim, -s, x, 1.0, v, c->st);
+  // P = 1 - Q Q^T over an orthonormal basis Q of x and the other roots' vectors: the
+  // correction stays away from every approximate eigenvector, so the other roots'
+  // near-singular directions of (A - w) do not enter the inner solve
+  int q = 0;
+  auto project = [&](double* v) {
+    std::vector<double> s = gram(c, Q.p, dim, q, v, dim, 1);
+    std::vector<double> coef(q);
+    for (int i = 0; i < q; ++i) coef[i] = -s[i];
+    lincomb(c, Q.p, dim, q, coef, v, dim, 1, true);
   };
   int n = 0;
   double last = 1e300;
   for (int outer = 0; outer < 8; ++outer) {
     const double nx = std::sqrt(gram(c, x, dim, 1, x, dim, 1)[0]);
     launch_axpby(dim, 1.0 / nx, x, 0.0, x, c->st);
+    q = 0;
+    CUDA_OK(cudaMemcpyAsync(Q.p, x, dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    q = 1;
+    for (const double* y : others) {
+      double* dst = Q.p + q * dim;
+      CUDA_OK(cudaMemcpyAsync(dst, y, dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+      for (int pass = 0; pass < 2; ++pass) project(dst);
+      const double ny = std::sqrt(std::max(gram(c, dst, dim, 1, dst, dim, 1)[0], 0.0));
+      if (ny > 1e-8) {
+        launch_axpby(dim, 1.0 / ny, dst, 0.0, dst, c->st);
+        ++q;
+      }
+    }
     {
       PrecScope fp64(c, CCSD_PREC_FP64);
       transform(x, ax.p);
@@ -705,7 +733,9 @@ int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol) {
     if (rn < tol) return n;
     if (!(rn < 0.5 * last)) throw Err(CCSD_ERR_NOT_CONVERGED, "eigenpair refinement stalled");
     last = rn;
-    // inner: P (A - w) P d = -r at the mixed precision
+    // inner: P (A - w) P d = -P r at the mixed precision
+    project(r.p);
+    const double rpn = std::sqrt(std::max(gram(c, r.p, dim, 1, r.p, dim, 1)[0], 0.0));
     launch_precond(c->vs, c->eps.p, r.p, d.p, w, c->st);
     launch_axpby(dim, 0.0, d.p, -1.0, d.p, c->st);
     project(d.p);
@@ -719,7 +749,7 @@ int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol) {
       launch_axpby(dim, 1.0, r.p, 1.0, res.p, c->st);
       const double en = std::sqrt(std::max(gram(c, res.p, dim, 1, res.p, dim, 1)[0], 0.0));
       if (verbose_solvers()) fprintf(stderr, "[refine side %d]   inner %d: |res| = %.3e\n", side, it, en);
-      if (en < 1e-4 * rn || en < 0.1 * tol) break;
+      if (en < 1e-4 * rpn || en < 0.1 * tol) break;
       launch_precond(c->vs, c->eps.p, res.p, dn.p, w, c->st);
       launch_axpby(dim, 1.0, d.p, -1.0, dn.p, c->st);  // dn = d - res / (D - w)
       project(dn.p);

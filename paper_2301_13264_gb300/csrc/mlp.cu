@@ -201,6 +201,17 @@ __global__ void k_sample(int64_t* idx, int batch, int64_t n, unsigned long long 
 // ---------------------------------------------------------------------------
 constexpr int TILE_BYTES = 128 * 64 * 2;  // one 128-row x 64-column bf16 chunk
 
+// tanh(x) = 1 - 2 / (exp(2x) + 1) with the hardware base-2 exponential and reciprocal
+// approximations (absolute error ~1e-7, below the bf16 spacing of the activations);
+// |x| is clamped at 9, where tanh is 1 to FP32 precision.
+__device__ __forceinline__ float fast_tanh(float x) {
+  const float xc = fminf(fmaxf(x, -9.f), 9.f);
+  float e, r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(xc * 2.8853900817779268f));  // 2 / ln 2
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(e + 1.f));
+  return fmaf(-2.f, r, 1.f);
+}
+
 // byte offset of element (row, k) (k < 64) in a 128B-swizzled chunk
 __device__ __forceinline__ uint32_t swz(int row, int k) {
   return (uint32_t)(row * 128 + ((((k >> 3) ^ row) & 7) << 4) + ((k & 7) << 1));
@@ -265,9 +276,9 @@ __global__ void __launch_bounds__(H, 2)
       uint32_t pk[4];
       for (int q = 0; q < 4; ++q) {
         const int k = k0 + 2 * q;
-        const float h0 = tanhf(sW1[k * 3] * x[0] + sW1[k * 3 + 1] * x[1] + sW1[k * 3 + 2] * x[2] + sb1[k]);
-        const float h1 =
-            tanhf(sW1[(k + 1) * 3] * x[0] + sW1[(k + 1) * 3 + 1] * x[1] + sW1[(k + 1) * 3 + 2] * x[2] + sb1[k + 1]);
+        const float h0 = fast_tanh(sW1[k * 3] * x[0] + sW1[k * 3 + 1] * x[1] + sW1[k * 3 + 2] * x[2] + sb1[k]);
+        const float h1 = fast_tanh(sW1[(k + 1) * 3] * x[0] + sW1[(k + 1) * 3 + 1] * x[1] + sW1[(k + 1) * 3 + 2] * x[2] +
+                                   sb1[k + 1]);
         __nv_bfloat162 v = __floats2bfloat162_rn(h0, h1);
         pk[q] = *reinterpret_cast<uint32_t*>(&v);
       }
@@ -302,7 +313,7 @@ __global__ void __launch_bounds__(H, 2)
       uint32_t r[32];
       tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
 #pragma unroll
-      for (int j = 0; j < 32; ++j) y += sw3[c + j] * tanhf(__uint_as_float(r[j]) + sb2[c + j]);
+      for (int j = 0; j < 32; ++j) y = fmaf(sw3[c + j], fast_tanh(__uint_as_float(r[j]) + sb2[c + j]), y);
     }
     if (row < n) out[row] = y * tscale;
     tc::fence_before();

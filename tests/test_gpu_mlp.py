@@ -53,13 +53,16 @@ def test_predict_matches_oracle_with_bf16_weights(n):
     out = np.zeros(n, dtype=np.float32)
     b.ccsd_mlp_predict(m, X, out)
     ref = omlp.forward_inference(m, X)
-    # bf16 weights and bf16 first-layer activations on both sides; FP32 accumulation and
-    # FP32 tanh in the kernel.  An activation within FP32 rounding of a bf16 tie may round
-    # the other way (about 2^-15 of them): allow a few such flips per row, plus FP32 noise.
+    # bf16 weights and bf16 first-layer activations on both sides; FP32 accumulation in
+    # the kernel and tanh from the hardware exponential and reciprocal (absolute error
+    # below 1e-6).  An activation within that error of a bf16 tie may round the other
+    # way: allow a few such flips per row, plus the tanh error through w3 and FP32 noise.
     err = np.abs(out - ref)
-    assert err.max() <= 3 * omlp.inference_flip_bound(m) + 2e-5 * np.abs(ref).max(), err.max()
-    # almost every row agrees to FP32 accumulation accuracy
-    assert np.quantile(err, 0.99) <= 2e-5 * np.abs(ref).max()
+    w3 = np.abs(omlp.bf16_weights(m)[512 + 128 * 128 + 128:512 + 128 * 128 + 256]).sum()
+    noise = 1e-6 * w3 * abs(m[-1]) + 2e-5 * np.abs(ref).max()
+    assert err.max() <= 3 * omlp.inference_flip_bound(m) + noise, err.max()
+    # almost every row carries no flip
+    assert np.quantile(err, 0.98) <= noise
 
 
 def test_features_match_oracle():
