@@ -607,8 +607,7 @@ int davidson(ccsd_ctx* c, int side, int nroots, std::vector<double>& omega, std:
   return d.iterations;
 }
 
-int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol,
-                     const std::vector<const double*>& others);
+int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol);
 
 // CCSD_VERBOSE=1: solver progress on stderr
 bool verbose_solvers() {
@@ -626,12 +625,7 @@ int refine_roots(ccsd_ctx* c, int side, std::vector<double>& w, std::vector<std:
   const int nroots = (int)w.size();
   int n = 0;
   try {
-    for (int k = 0; k < nroots; ++k) {
-      std::vector<const double*> others;
-      for (int j = 0; j < nroots; ++j)
-        if (j != k) others.push_back(vecs[j]->p);
-      n += refine_eigenpair(c, side, vecs[k]->p, w[k], c->opt.tol_eom, others);
-    }
+    for (int k = 0; k < nroots; ++k) n += refine_eigenpair(c, side, vecs[k]->p, w[k], c->opt.tol_eom);
     return n;
   } catch (const Err& e) {
     if (e.code != CCSD_ERR_NOT_CONVERGED) throw;
@@ -673,52 +667,34 @@ int davidson_refined(ccsd_ctx* c, int side, int nroots, std::vector<double>& w,
 
 // Defect correction of one eigenpair (x, w) of A (side 0) or A^T (side 1) to the FP64
 // residual tolerance: per outer step one FP64 transform gives r = A x - w x (w the
-// Rayleigh quotient of the unit vector x); the correction d solves the projected
-// equation P (A - w) P d = -P r, P = 1 - Q Q^T with Q an orthonormal basis of x and
-// the other roots' vectors (deflation), by preconditioned Jacobi + DIIS with
-// transforms at the handle's (mixed) precision, to 1e-4 of |P r|;
-// x += d.  Each step gains the mixed operator's accuracy (~5 digits), so two or three
-// FP64 transforms per root replace an FP64 Davidson continuation.  Returns the number
-// of transforms (FP64 + mixed); throws if the residual stops decreasing.
-int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol,
-                     const std::vector<const double*>& others) {
+// Rayleigh quotient of the unit vector x); the correction d (d perpendicular to x)
+// solves the projected equation P (A - w) P d = -r, P = 1 - x x^T (the Jacobi-Davidson
+// correction equation), by right-preconditioned restarted GMRES with transforms at the
+// handle's (mixed) precision and the preconditioner (D - w)^-1, to 1e-4 of |r|; x += d.
+// For a root above the lowest, (A - w) is indefinite on the complement of x (the lower
+// roots give negative eigenvalues), which GMRES handles; each outer step gains the
+// mixed operator's accuracy, so two or three FP64 transforms per root replace an FP64
+// Davidson continuation.  Returns the transforms used; throws if |r| stops decreasing.
+int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol) {
   const int64_t dim = c->dim;
-  const int nq = 1 + (int)others.size();
-  DevBuf ax(dim), r(dim), d(dim), ad(dim), res(dim), dn(dim), Q(nq * dim);
+  constexpr int KR = 16;  // Krylov vectors per restart
+  DevBuf ax(dim), r(dim), z(dim), u(dim), V((KR + 1) * dim);
   auto transform = [&](const double* in, double* out) {
     if (side == 0)
       right_block(c, in, out, 1);
     else
       left_block(c, in, out, 1);
   };
-  // P = 1 - Q Q^T over an orthonormal basis Q of x and the other roots' vectors: the
-  // correction stays away from every approximate eigenvector, so the other roots'
-  // near-singular directions of (A - w) do not enter the inner solve
-  int q = 0;
-  auto project = [&](double* v) {
-    std::vector<double> s = gram(c, Q.p, dim, q, v, dim, 1);
-    std::vector<double> coef(q);
-    for (int i = 0; i < q; ++i) coef[i] = -s[i];
-    lincomb(c, Q.p, dim, q, coef, v, dim, 1, true);
+  auto project = [&](double* v) {  // v -= x <x|v>
+    const double s = gram(c, x, dim, 1, v, dim, 1)[0];
+    launch_axpby(dim, -s, x, 1.0, v, c->st);
   };
+  auto norm = [&](const double* v) { return std::sqrt(std::max(gram(c, v, dim, 1, v, dim, 1)[0], 0.0)); };
   int n = 0;
   double last = 1e300;
   for (int outer = 0; outer < 8; ++outer) {
-    const double nx = std::sqrt(gram(c, x, dim, 1, x, dim, 1)[0]);
+    const double nx = norm(x);
     launch_axpby(dim, 1.0 / nx, x, 0.0, x, c->st);
-    q = 0;
-    CUDA_OK(cudaMemcpyAsync(Q.p, x, dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-    q = 1;
-    for (const double* y : others) {
-      double* dst = Q.p + q * dim;
-      CUDA_OK(cudaMemcpyAsync(dst, y, dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-      for (int pass = 0; pass < 2; ++pass) project(dst);
-      const double ny = std::sqrt(std::max(gram(c, dst, dim, 1, dst, dim, 1)[0], 0.0));
-      if (ny > 1e-8) {
-        launch_axpby(dim, 1.0 / ny, dst, 0.0, dst, c->st);
-        ++q;
-      }
-    }
     {
       PrecScope fp64(c, CCSD_PREC_FP64);
       transform(x, ax.p);
@@ -727,35 +703,86 @@ int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol,
     w = gram(c, x, dim, 1, ax.p, dim, 1)[0];
     launch_axpby(dim, 1.0, ax.p, 0.0, r.p, c->st);
     launch_axpby(dim, -w, x, 1.0, r.p, c->st);
-    const double rn = std::sqrt(std::max(gram(c, r.p, dim, 1, r.p, dim, 1)[0], 0.0));
+    const double rn = norm(r.p);
     if (verbose_solvers())
       fprintf(stderr, "[refine side %d] outer %d: w = %.12f, |r| = %.3e (%d transforms so far)\n", side, outer, w, rn, n);
     if (rn < tol) return n;
     if (!(rn < 0.5 * last)) throw Err(CCSD_ERR_NOT_CONVERGED, "eigenpair refinement stalled");
     last = rn;
-    // inner: P (A - w) P d = -P r at the mixed precision
-    project(r.p);
-    const double rpn = std::sqrt(std::max(gram(c, r.p, dim, 1, r.p, dim, 1)[0], 0.0));
-    launch_precond(c->vs, c->eps.p, r.p, d.p, w, c->st);
-    launch_axpby(dim, 0.0, d.p, -1.0, d.p, c->st);
-    project(d.p);
-    Diis diis(c, c->opt.diis_dim);
-    for (int it = 0; it < 60; ++it) {
-      transform(d.p, ad.p);
+    // GMRES on Op(v) = P (A - w) P M^-1 v, Op(q) = -r, d = P M^-1 q (q accumulated in u)
+    auto op = [&](const double* v, double* out) {
+      launch_precond(c->vs, c->eps.p, v, z.p, w, c->st);  // z = M^-1 v
+      project(z.p);
+      transform(z.p, out);
       ++n;
-      launch_axpby(dim, 1.0, ad.p, 0.0, res.p, c->st);
-      launch_axpby(dim, -w, d.p, 1.0, res.p, c->st);
-      project(res.p);
-      launch_axpby(dim, 1.0, r.p, 1.0, res.p, c->st);
-      const double en = std::sqrt(std::max(gram(c, res.p, dim, 1, res.p, dim, 1)[0], 0.0));
-      if (verbose_solvers()) fprintf(stderr, "[refine side %d]   inner %d: |res| = %.3e\n", side, it, en);
-      if (en < 1e-4 * rpn || en < 0.1 * tol) break;
-      launch_precond(c->vs, c->eps.p, res.p, dn.p, w, c->st);
-      launch_axpby(dim, 1.0, d.p, -1.0, dn.p, c->st);  // dn = d - res / (D - w)
-      project(dn.p);
-      diis.step(dn.p, res.p, d.p);
+      launch_axpby(dim, -w, z.p, 1.0, out, c->st);
+      project(out);
+    };
+    CUDA_OK(cudaMemsetAsync(u.p, 0, dim * sizeof(double), c->st));
+    const double target = std::max(1e-4 * rn, 0.1 * tol);
+    double resid = rn;
+    for (int cycle = 0; cycle < 4 && resid > target; ++cycle) {
+      // v0 = (-r - Op(u)) / beta
+      double* v0 = V.p;
+      launch_axpby(dim, -1.0, r.p, 0.0, v0, c->st);
+      if (cycle > 0) {
+        op(u.p, ax.p);
+        launch_axpby(dim, -1.0, ax.p, 1.0, v0, c->st);
+      }
+      const double beta = norm(v0);
+      if (!(beta > target)) break;
+      launch_axpby(dim, 1.0 / beta, v0, 0.0, v0, c->st);
+      std::vector<double> Hm((KR + 1) * KR, 0.0), cs(KR), sn(KR), g(KR + 1, 0.0);
+      g[0] = beta;
+      int k = 0;
+      for (; k < KR; ++k) {
+        double* vk1 = V.p + (k + 1) * dim;
+        op(V.p + k * dim, vk1);
+        // modified Gram-Schmidt against V[0..k], twice
+        for (int pass = 0; pass < 2; ++pass) {
+          std::vector<double> hcol = gram(c, V.p, dim, k + 1, vk1, dim, 1);
+          std::vector<double> coef(k + 1);
+          for (int i = 0; i <= k; ++i) {
+            Hm[i * KR + k] += hcol[i];
+            coef[i] = -hcol[i];
+          }
+          lincomb(c, V.p, dim, k + 1, coef, vk1, dim, 1, true);
+        }
+        const double hn = norm(vk1);
+        Hm[(k + 1) * KR + k] = hn;
+        for (int j = 0; j < k; ++j) {
+          const double a = Hm[j * KR + k], b = Hm[(j + 1) * KR + k];
+          Hm[j * KR + k] = cs[j] * a + sn[j] * b;
+          Hm[(j + 1) * KR + k] = -sn[j] * a + cs[j] * b;
+        }
+        const double a = Hm[k * KR + k], b = Hm[(k + 1) * KR + k];
+        const double den = std::hypot(a, b);
+        cs[k] = den > 0 ? a / den : 1.0;
+        sn[k] = den > 0 ? b / den : 0.0;
+        Hm[k * KR + k] = den;
+        Hm[(k + 1) * KR + k] = 0.0;
+        g[k + 1] = -sn[k] * g[k];
+        g[k] = cs[k] * g[k];
+        resid = std::fabs(g[k + 1]);
+        if (verbose_solvers()) fprintf(stderr, "[refine side %d]   gmres %d.%d: |res| = %.3e\n", side, cycle, k, resid);
+        if (hn > 0) launch_axpby(dim, 1.0 / hn, vk1, 0.0, vk1, c->st);
+        if (resid <= target || hn == 0.0) {
+          ++k;
+          break;
+        }
+      }
+      std::vector<double> y(k, 0.0);
+      for (int j = k - 1; j >= 0; --j) {
+        double s = g[j];
+        for (int q = j + 1; q < k; ++q) s -= Hm[j * KR + q] * y[q];
+        y[j] = s / Hm[j * KR + j];
+      }
+      lincomb(c, V.p, dim, k, y, u.p, dim, 1, true);
     }
-    launch_axpby(dim, 1.0, d.p, 1.0, x, c->st);
+    // d = P M^-1 u
+    launch_precond(c->vs, c->eps.p, u.p, z.p, w, c->st);
+    project(z.p);
+    launch_axpby(dim, 1.0, z.p, 1.0, x, c->st);
   }
   throw Err(CCSD_ERR_NOT_CONVERGED, "eigenpair refinement did not converge");
 }
