@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -14,6 +15,7 @@
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/ccsd.h"
@@ -315,7 +317,7 @@ int solve_right_linear(ccsd_ctx* c, const double* rhs, double* x, double tol, in
   return maxit;
 }
 
-int solve_left_linear(ccsd_ctx* c, const double* rhs, double* x, double tol);
+int solve_left_linear(ccsd_ctx* c, const double* rhs, double* x, double tol, bool stall_ok = false);
 
 // x^T A = -rhs^T to the FP64 tolerance: in mixed mode with refinement the
 // equations are first solved in mixed precision to tol_switch, then corrected:
@@ -323,7 +325,7 @@ int solve_left_linear(ccsd_ctx* c, const double* rhs, double* x, double tol);
 // precision to a fraction of |rho|, x += d, until max |rho| < tol.
 int solve_left_refined(ccsd_ctx* c, const double* rhs, double* x, double tol) {
   if (!refining(c)) return solve_left_linear(c, rhs, x, tol);
-  int it = solve_left_linear(c, rhs, x, std::max(tol, c->opt.tol_switch));
+  int it = solve_left_linear(c, rhs, x, std::max(tol, c->opt.tol_switch), true);
   DevBuf rho(c->dim), d(c->dim);
   for (int outer = 0; outer < 20; ++outer) {
     {
@@ -337,22 +339,33 @@ int solve_left_refined(ccsd_ctx* c, const double* rhs, double* x, double tol) {
     if (err < tol) return it;
     launch_precond(c->vs, c->eps.p, rho.p, d.p, 0.0, c->st);
     launch_axpby(c->dim, 0.0, d.p, -1.0, d.p, c->st);
-    it += solve_left_linear(c, rho.p, d.p, std::max(1e-3 * err, 0.1 * tol));
+    it += solve_left_linear(c, rho.p, d.p, std::max(1e-3 * err, 0.1 * tol), true);
     launch_axpby(c->dim, 1.0, d.p, 1.0, x, c->st);
   }
   throw Err(CCSD_ERR_NOT_CONVERGED, "FP64 refinement of the linear equations did not converge");
 }
 
-// Solve x^T A = -rhs^T by preconditioned Jacobi + DIIS; x holds the guess on entry
-int solve_left_linear(ccsd_ctx* c, const double* rhs, double* x, double tol) {
+// Solve x^T A = -rhs^T by preconditioned Jacobi + DIIS; x holds the guess on entry.
+// With stall_ok (the mixed phase before an FP64 refinement) the iteration also stops
+// once it no longer halves the residual in 8 iterations within 100 tol: the
+// mixed-precision floor, from where the refinement continues.
+int solve_left_linear(ccsd_ctx* c, const double* rhs, double* x, double tol, bool stall_ok) {
   DevBuf res(c->dim), xn(c->dim);
   Diis diis(c, c->opt.diis_dim);
+  double best = 1e300;
+  int since_best = 0;
   for (int it = 1; it <= c->opt.max_iter; ++it) {
     left_block(c, x, res.p, 1);
     launch_axpby(c->dim, 1.0, rhs, 1.0, res.p, c->st);
     double err = maxabs(c, res.p, c->dim);
     if (!std::isfinite(err)) throw Err(CCSD_ERR_NOT_CONVERGED, "linear equations diverged");
     if (err < tol) return it;
+    if (err < 0.5 * best) {
+      best = err;
+      since_best = 0;
+    } else if (stall_ok && ++since_best >= 8 && err < 100.0 * tol) {
+      return it;
+    }
     launch_precond(c->vs, c->eps.p, res.p, xn.p, 0.0, c->st);
     launch_axpby(c->dim, 1.0, x, -1.0, xn.p, c->st);  // xn = x - res/D
     diis.step(xn.p, res.p, x);
@@ -1907,6 +1920,35 @@ ccsd_status batch_guarded(ccsd_batch_ctx* b, F&& f) {
   }
 }
 
+// f(i) for i < n on up to hardware_concurrency host threads (each system's host-side
+// solver work runs on its own stream, so systems proceed independently); the first
+// exception is rethrown after all threads have joined
+template <typename F>
+void parallel_for(int n, F&& f) {
+  int dev = 0;
+  CUDA_OK(cudaGetDevice(&dev));
+  const int nt = std::max(1, std::min<int>(n, (int)std::max(1u, std::thread::hardware_concurrency())));
+  std::atomic<int> next{0};
+  std::vector<std::exception_ptr> err(n);
+  std::vector<std::thread> th;
+  for (int t = 0; t < nt; ++t)
+    th.emplace_back([&] {
+      cudaSetDevice(dev);
+      for (;;) {
+        const int i = next++;
+        if (i >= n) break;
+        try {
+          f(i);
+        } catch (...) {
+          err[i] = std::current_exception();
+        }
+      }
+    });
+  for (auto& t : th) t.join();
+  for (auto& e : err)
+    if (e) std::rethrow_exception(e);
+}
+
 // system s's block transform of its staging vectors, on its own stream, without synchronising
 void batch_block(ccsd_batch_ctx* b, int s, int side) {
   ccsd_ctx* c = b->sys[s];
@@ -2087,12 +2129,12 @@ ccsd_status ccsd_batch_eom_solve(ccsd_batch b, int side, int nroots, double* ome
         throw Err(CCSD_ERR_STATE, "side 1 needs the right solve with the same nroots first");
     }
     std::vector<std::unique_ptr<Davidson>> d(ns);
-    for (int s = 0; s < ns; ++s) {
+    parallel_for(ns, [&](int s) {
       ccsd_ctx* c = b->sys[s];
       const double tol = refining(c) ? std::max(c->opt.tol_eom, 10.0 * c->opt.tol_switch) : c->opt.tol_eom;
       d[s].reset(new Davidson(c, side, nroots, tol, side == 1 ? &c->R : nullptr));
       if (side == 1) d[s]->targets = c->omega;
-    }
+    });
     std::vector<char> done(ns, 0), mask(ns, 1);
     std::vector<int> it(ns, 0);
     int left = ns;
@@ -2126,14 +2168,17 @@ ccsd_status ccsd_batch_eom_solve(ccsd_batch b, int side, int nroots, double* ome
             off[s] += k[s];
           }
       }
-      for (int s = 0; s < ns; ++s) {
-        if (done[s]) continue;
+      std::vector<char> conv(ns, 0);
+      parallel_for(ns, [&](int s) {
+        if (done[s]) return;
         CUDA_OK(cudaStreamSynchronize(b->sys[s]->st));
-        if (d[s]->advance()) {
+        conv[s] = d[s]->advance() ? 1 : 0;
+      });
+      for (int s = 0; s < ns; ++s)
+        if (!done[s] && conv[s]) {
           done[s] = 1;
           --left;
         }
-      }
       // drop converged systems from the launched set once a quarter of it is idle
       int active = 0, idle = 0;
       for (int s = 0; s < ns; ++s)
@@ -2142,7 +2187,7 @@ ccsd_status ccsd_batch_eom_solve(ccsd_batch b, int side, int nroots, double* ome
         for (int s = 0; s < ns; ++s)
           if (done[s]) mask[s] = 0;
     }
-    for (int s = 0; s < ns; ++s) {
+    parallel_for(ns, [&](int s) {
       ccsd_ctx* c = b->sys[s];
       std::vector<double> w = d[s]->omega;
       int its = d[s]->iterations;
@@ -2158,7 +2203,7 @@ ccsd_status ccsd_batch_eom_solve(ccsd_batch b, int side, int nroots, double* ome
       }
       if (omega) std::copy(w.begin(), w.end(), omega + (size_t)s * nroots);
       if (iters) iters[s] = its;
-    }
+    });
   });
 }
 
