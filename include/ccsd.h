@@ -155,8 +155,9 @@ ccsd_status ccsd_derivative_coupling(ccsd_handle h, int k, int l, int ndir, cons
  * The nearest Hartree-Fock orbitals to the given orthonormal ones: U = exp(K) with
  * K[a][i] = kappa[i][a] = -K[i][a] (occupied-virtual rotations only), kappa solving
  * F(U^T h U, U^T B U)_ia = 0 (closed-shell Fock matrix, Lagrangian section) by
- * Newton-type steps (A^HF d-kappa = -F' at the current orbitals, conjugate
- * gradients, preconditioner 1/(eps_a - eps_i)) until max |F'_ia| < tol.  Returns
+ * Newton-type steps (J d-kappa = -F' with J = dF'/dkappa at the current orbitals,
+ * by GMRES with the preconditioner 1/(eps_a - eps_i); J is not symmetric away from
+ * the solution) until max |F'_ia| < tol.  Returns
  * U[n*n] and, when not NULL, the rotated integrals h_out[n*n], B_out[naux*n*n].
  * Arrays may be host or device memory.  CCSD_ERR_NOT_CONVERGED after 100 steps. */
 ccsd_status ccsd_scf(const double* eps, const double* h, const double* B, int o, int v, int naux, double tol,

@@ -15,7 +15,8 @@ Paper passages followed:
   t-eta (Eq. for t-eta and its CCSD first term), zeta^T A = -t-eta^T (Eq.
   amplituderelax), and F^q = <L_i|[Hbar^q, R_j]|HF>/(omega_j - omega_i) +
   <zeta|Hbar^q|HF> (Eq. NAC_NC) with the orbital term absent because the
-  orbitals are fixed and x-independent; for j = 0, zeta = L_i/(E_0 - E_i) and
+  orbitals are fixed and x-independent (the relaxed-orbital form, with HF
+  orbitals that follow x, is in relaxed.py); for j = 0, zeta = L_i/(E_0 - E_i) and
   F_i0 = <zeta|Hbar^q|HF> (Eqs. for the ground-state right state);
 * the definition F_ij = <psi_i^L | d/dx psi_j^R> (Eq. nac), evaluated by central
   differences of O_ij(x) = <psi_i^L(x0)|psi_j^R(x)> with the normalisation

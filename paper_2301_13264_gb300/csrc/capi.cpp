@@ -146,6 +146,7 @@ void lincomb(ccsd_ctx* c, const double* X, int64_t ldx, int np, const std::vecto
 double forward(ccsd_ctx* c, const double* t, double* om) {
   auto& cp = c->P.cp;
   Executor& ex = *c->ex;
+  ex.invalidate_frozen();  // new amplitudes: slices of the old ones and their intermediates are stale
   ex.set_nvec(1);
   ex.bind(cp.t1, const_cast<double*>(t));
   ex.bind(cp.t2, const_cast<double*>(t) + c->n1);
@@ -1357,6 +1358,11 @@ ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int
     ex.ladder_w_ = cp.g.id("W");
     ex.const_tensors = {cp.h, cp.B, cp.ones_o};
     for (const Op& op : cp.fwd_const) ex.const_tensors.insert(op.out.t);
+    // the amplitudes and the intermediates computed from them change only when the
+    // forward program runs again (forward() drops their cached slices first)
+    ex.frozen_tensors = {cp.t1, cp.t2};
+    for (const Op& op : cp.fwd_t)
+      if (op.out.t != cp.O1 && op.out.t != cp.O2 && op.out.t != cp.E) ex.frozen_tensors.insert(op.out.t);
     {
       // under FP64 refinement the Hamiltonian-only intermediates are built in FP64,
       // so that the refined equations are exactly the FP64 ones
@@ -1891,6 +1897,7 @@ struct ccsd_batch_ctx {
     std::vector<char> mask;
     cudaGraphExec_t exec;
     long long nodes;
+    std::vector<uint64_t> epochs;  // the systems' operand-cache epochs at capture
   };
   std::vector<Graph> graphs;
   long long launches = 0, captures = 0, last_nodes = 0;
@@ -1978,6 +1985,17 @@ void batch_run(ccsd_batch_ctx* b, int side, const std::vector<char>& mask) {
         b->G[s].reset(new DevBuf(b->nvec * b->sys[s]->dim));
       }
     }
+  std::vector<uint64_t> epochs(ns);
+  for (int s = 0; s < ns; ++s) epochs[s] = b->sys[s]->ex->cache_epoch();
+  // graphs whose captured operand slices were dropped since (new amplitudes) are stale
+  for (size_t i = 0; i < b->graphs.size();) {
+    if (b->graphs[i].epochs != epochs) {
+      cudaGraphExecDestroy(b->graphs[i].exec);
+      b->graphs.erase(b->graphs.begin() + i);
+    } else {
+      ++i;
+    }
+  }
   for (auto& g : b->graphs)
     if (g.side == side && g.mask == mask) {
       CUDA_OK(cudaGraphLaunch(g.exec, b->cap));
@@ -2028,7 +2046,8 @@ void batch_run(ccsd_batch_ctx* b, int side, const std::vector<char>& mask) {
   CUDA_OK(e);
   ++b->captures;
   b->last_nodes = (long long)nnodes;
-  b->graphs.push_back({side, mask, exec, (long long)nnodes});
+  for (int s = 0; s < ns; ++s) epochs[s] = b->sys[s]->ex->cache_epoch();
+  b->graphs.push_back({side, mask, exec, (long long)nnodes, epochs});
 }
 
 void batch_release(ccsd_batch_ctx* b) {

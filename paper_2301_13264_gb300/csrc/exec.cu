@@ -276,7 +276,10 @@ void Executor::exec_contract(const Op& op) {
       return g;
     };
     Strided ag = gather(ea, Ml), bg = gather(eb, Nl);
-    const bool a_const = const_tensors.count(op.a.t) > 0, b_const = const_tensors.count(op.b.t) > 0;
+    // amplitude-dependent operands are cached only in runs that leave all of them unchanged
+    // (the derivative programs), not in the forward program that recomputes them
+    auto cacheable = [&](int t) { return const_tensors.count(t) > 0 || (frozen_tensors.count(t) > 0 && !frozen_run_); };
+    const bool a_const = cacheable(op.a.t), b_const = cacheable(op.b.t);
     // non-contiguous outputs are addressed by the GEMM epilogue through the output's own strides
     Strided om, on;
     auto out_dims = [&](const std::vector<char>& labels, Strided& g) {
@@ -508,6 +511,13 @@ void Executor::run(const Prog& p) {
     if (op.kind == 'C') last_use[op.b.t] = i;
   }
   const int64_t tc_calls_at_start = stats.tc_calls;
+  // slices cached for amplitude-dependent tensors this run rewrites are stale
+  frozen_run_ = false;
+  for (const Op& op : p)
+    if (frozen_tensors.count(op.out.t)) {
+      frozen_run_ = true;
+      if (ts_[op.out.t].p) drop_cache_range(ts_[op.out.t].p, numel(op.out.t));
+    }
   std::set<int> run_temps;
   for (auto& kv : first_write) {
     int t = kv.first;

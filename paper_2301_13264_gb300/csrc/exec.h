@@ -161,6 +161,15 @@ class Executor {
   int tc_error();
   // tensors whose values never change after set-up (their bf16 slices may be cached)
   std::set<int> const_tensors;
+  // tensors that change only with the amplitudes (the primal intermediates and the
+  // amplitudes themselves): their bf16 slices are kept across runs of the derivative
+  // programs, which leave them unchanged, until invalidate_frozen() is called because
+  // the amplitudes changed
+  std::set<int> frozen_tensors;
+  void invalidate_frozen();
+  // changes whenever cached operand slices are dropped (graphs that captured their
+  // addresses must then be captured again)
+  uint64_t cache_epoch() const { return cache_epoch_; }
   // Profiling: when on, every GEMM launch is bracketed by CUDA events on the
   // executor's stream; collect() returns per-engine totals and clears the records.
   struct ProfTotals {
@@ -176,6 +185,11 @@ class Executor {
   double last_tc_issued = 0.0;  // MMA flops of the last tensor-core launch (padding included)
   struct CacheEntry;
   std::vector<CacheEntry*> cache_;
+
+ private:
+  bool frozen_run_ = false;  // the current run writes amplitude-dependent tensors
+  uint64_t cache_epoch_ = 0;
+  void drop_cache_range(const double* p, int64_t n);
 };
 
 // A device-side wait exceeded its budget (the kernel raised its error flag).

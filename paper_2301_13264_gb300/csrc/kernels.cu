@@ -57,9 +57,105 @@ __global__ void k_zero_strided(double* __restrict__ dst, Strided sp, I total) {
   }
 }
 
+// Permuted add / copy whose destination and source are contiguous along different
+// dimensions da and db: 32 x 32 tiles over (da, db) staged through shared memory, so
+// reads run along the source's contiguous dimension and writes along the
+// destination's; the other dimensions' offsets are decomposed once per tile.
+template <bool COPY>
+__global__ void __launch_bounds__(256) k_axpy_transpose(double* __restrict__ dst, const double* __restrict__ src,
+                                                        Strided sp, int da, int db, int tiles_a, int tiles_b,
+                                                        double alpha) {
+  __shared__ double tile[32][33];
+  int64_t blk = blockIdx.x;
+  const int tbi = (int)(blk % tiles_b);
+  blk /= tiles_b;
+  const int tai = (int)(blk % tiles_a);
+  int64_t rest = blk / tiles_a;
+  int64_t o0 = 0, o1 = 0;
+  for (int d = sp.ndim - 1; d >= 0; --d) {
+    if (d == da || d == db) continue;
+    const int64_t e = sp.ext[d], c = rest % e;
+    rest /= e;
+    o0 += c * sp.s0[d];
+    o1 += c * sp.s1[d];
+  }
+  const int64_t ea = sp.ext[da], eb = sp.ext[db];
+  const int64_t src_a = sp.s1[da], dst_b = sp.s0[db];
+  const int a0 = tai * 32, b0 = tbi * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {  // read along b (source-contiguous)
+    const int64_t a = a0 + i, b = b0 + threadIdx.x;
+    if (a < ea && b < eb) tile[i][threadIdx.x] = src[o1 + a * src_a + b];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {  // write along a (destination-contiguous)
+    const int64_t b = b0 + i, a = a0 + threadIdx.x;
+    if (a < ea && b < eb) {
+      const double v = tile[threadIdx.x][i];
+      double* p = dst + o0 + a + b * dst_b;
+      if (COPY)
+        *p = v;
+      else
+        *p += alpha * v;
+    }
+  }
+}
+
+// The same when both are contiguous along one dimension d0: one block per row of the
+// other dimensions (offsets decomposed once per row), threads along d0.
+template <bool COPY>
+__global__ void __launch_bounds__(256) k_axpy_rows(double* __restrict__ dst, const double* __restrict__ src,
+                                                   Strided sp, int d0, int64_t rows, double alpha) {
+  const int64_t ed = sp.ext[d0];
+  for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+    int64_t rest = row, o0 = 0, o1 = 0;
+    for (int d = sp.ndim - 1; d >= 0; --d) {
+      if (d == d0) continue;
+      const int64_t e = sp.ext[d], c = rest % e;
+      rest /= e;
+      o0 += c * sp.s0[d];
+      o1 += c * sp.s1[d];
+    }
+    for (int64_t k = threadIdx.x; k < ed; k += blockDim.x) {
+      if (COPY)
+        dst[o0 + k] = src[o1 + k];
+      else
+        dst[o0 + k] += alpha * src[o1 + k];
+    }
+  }
+}
+
+// dispatch to the tiled kernels when the layouts allow; false: use the general one
+template <bool COPY>
+static bool launch_axpy_fast(double* dst, const double* src, const Strided& sp, double alpha, cudaStream_t st) {
+  int da = -1, db = -1;
+  for (int d = 0; d < sp.ndim; ++d) {
+    if (sp.s0[d] == 1 && sp.ext[d] > 1) da = d;
+    if (sp.s1[d] == 1 && sp.ext[d] > 1) db = d;
+  }
+  if (da < 0 || db < 0) return false;
+  int64_t other = 1;
+  for (int d = 0; d < sp.ndim; ++d)
+    if (d != da && d != db) other *= sp.ext[d];
+  if (da == db) {
+    if (sp.ext[da] < 32) return false;
+    const int threads = sp.ext[da] >= 256 ? 256 : (sp.ext[da] >= 128 ? 128 : 64);
+    count_launches(1);
+    k_axpy_rows<COPY><<<(int)std::min<int64_t>(other, 152 * 64), threads, 0, st>>>(dst, src, sp, da, other, alpha);
+    return true;
+  }
+  if (sp.ext[da] < 8 || sp.ext[db] < 8) return false;
+  const int ta = (int)((sp.ext[da] + 31) / 32), tb = (int)((sp.ext[db] + 31) / 32);
+  const int64_t blocks = other * ta * tb;
+  if (blocks > 0x7fffffffLL) return false;
+  count_launches(1);
+  k_axpy_transpose<COPY><<<(unsigned)blocks, dim3(32, 8), 0, st>>>(dst, src, sp, da, db, ta, tb, alpha);
+  return true;
+}
+
 void launch_axpy_strided(double* dst, const double* src, const Strided& sp, double alpha, cudaStream_t st) {
   int64_t n = sp.total();
   if (n == 0) return;
+  if (launch_axpy_fast<false>(dst, src, sp, alpha, st)) return;
   count_launches(1);
   if (n < (int64_t(1) << 31))
     k_axpy_strided<uint32_t, false><<<grid_for(n), 256, 0, st>>>(dst, src, sp, (uint32_t)n, alpha);
@@ -70,6 +166,7 @@ void launch_axpy_strided(double* dst, const double* src, const Strided& sp, doub
 void launch_copy_strided(double* dst, const double* src, const Strided& sp, cudaStream_t st) {
   int64_t n = sp.total();
   if (n == 0) return;
+  if (launch_axpy_fast<true>(dst, src, sp, 1.0, st)) return;
   count_launches(1);
   if (n < (int64_t(1) << 31))
     k_axpy_strided<uint32_t, true><<<grid_for(n), 256, 0, st>>>(dst, src, sp, (uint32_t)n, 1.0);

@@ -309,12 +309,36 @@ static bool same_gather(const Strided& a, const Strided& b) {
   return true;
 }
 
+void Executor::drop_cache_range(const double* p, int64_t n) {
+  bool dropped = false;
+  for (size_t i = 0; i < cache_.size();) {
+    CacheEntry* e = cache_[i];
+    if (e->src >= p && e->src < p + n) {
+      cudaStreamSynchronize(st_);  // no kernel may still read the slices
+      cudaFree(e->dev);
+      cache_bytes_ -= e->bytes;
+      delete e;
+      cache_.erase(cache_.begin() + i);
+      dropped = true;
+    } else {
+      ++i;
+    }
+  }
+  if (dropped) ++cache_epoch_;
+}
+
+void Executor::invalidate_frozen() {
+  for (int t : frozen_tensors)
+    if (ts_[t].p) drop_cache_range(ts_[t].p, numel(t));
+}
+
 void Executor::clear_cache() {
   for (CacheEntry* e : cache_) {
     if (e->dev) cudaFree(e->dev);
     delete e;
   }
   cache_.clear();
+  ++cache_epoch_;
   for (WPM& w : wpm_) {
     if (w.plus) cudaFree(w.plus);
     if (w.minus) cudaFree(w.minus);
