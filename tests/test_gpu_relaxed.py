@@ -81,6 +81,9 @@ def test_relaxed_couplings_match_oracle(precision):
     for kl in pairs:
         ref, kb = rx.relaxed_coupling(S, res, kl[0], kl[1], h1o, B1o, tol_lin=1e-12)
         assert abs(F[kl] - ref) < 1e-7 * abs(ref) + 1e-10, (kl, F[kl], ref)
-        assert np.abs(KB[kl] - kb.numpy()).max() < 1e-7 * np.abs(kb.numpy()).max() + 1e-11
+        # kappa-bar is linear in the eigenvectors, so it carries their error to first
+        # order: an absolute error up to about the eigenvector residual tolerance.  The
+        # coupling is stationary in the multipliers and carries it only to second order.
+        assert np.abs(KB[kl] - kb.numpy()).max() < 1e-7 * np.abs(kb.numpy()).max() + kw["tol_eom"]
         # the orbital term is resolved
         assert abs(F[kl] - Fu[kl]) > 100 * abs(F[kl] - ref)
