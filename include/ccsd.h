@@ -83,6 +83,11 @@ typedef struct {
   double tol_switch;    /* mixed mode with refine: residual level at which the FP64 refinement starts */
   int autotune;         /* mixed mode: 1 = time the tensor-core tile widths and split counts once per GEMM
                            shape and keep the fastest; 0 = choose them from the output width */
+  int fp64_tc;          /* mixed mode: what the handle evaluates at FP64 accuracy (refinement residuals,
+                           Hamiltonian-only intermediates, densities) runs its contractions above
+                           tc_min_flops as FP64-grade tensor-core products (1, default: 7 fixed-point
+                           bf16 slices per operand, exact FP32 sums per K chunk, integer accumulation;
+                           error about 2^-46 max|A_m.| max|B_n.| per K term) or as FP64 DFMA (0) */
 } ccsd_options;
 
 /* Fill *opt with defaults (FP64, tol_res 1e-10, tol_eom 1e-7, tol_lin 1e-9, ...). */
@@ -255,6 +260,20 @@ ccsd_status ccsd_derivative_coupling_noalloc(ccsd_handle h, int k, int l, int nd
 /* Seconds spent in the last call and counters of the executor (GEMM calls,
  * tensor-core calls and their flops) since creation; any pointer may be NULL. */
 ccsd_status ccsd_stats(ccsd_handle h, double* flops_fp64, double* flops_tc, long long* gemms, long long* tc_gemms);
+
+/* One plain contraction C = alpha A B^T + beta C in one of the library's arithmetic forms,
+ * for tests and measurements: A (M x K), B (N x K) and C (M x N) are row-major HOST
+ * arrays (copied to and from the device; C read only when beta != 0).  form:
+ *   CCSD_GEMM_FP64     FP64 DFMA GEMM;
+ *   CCSD_GEMM_SPLIT    split-bf16 tensor-core products (splits 2 or 3, FP32 accumulation);
+ *   CCSD_GEMM_FP64_TC  FP64-grade tensor-core products (fixed-point slices, see fp64_tc).
+ * beta must be 0 or 1 for the tensor-core forms.  reps > 1 repeats the device GEMM reps
+ * times (inputs resident) and *ms (may be NULL) receives the mean device time of one, from
+ * CUDA events; operand preparation (slicing) is inside the timed region.  Errors:
+ * CCSD_ERR_ARG (sizes, form, beta), CCSD_ERR_OOM, CCSD_ERR_CUDA, CCSD_ERR_TIMEOUT. */
+enum { CCSD_GEMM_FP64 = 0, CCSD_GEMM_SPLIT = 1, CCSD_GEMM_FP64_TC = 2 };
+ccsd_status ccsd_gemm(int form, int splits, int M, int N, int K, double alpha, const double* A, const double* B,
+                      double beta, double* C, int reps, double* ms);
 
 /* Kernel-level profile of the calls made between ccsd_profile_start and
  * ccsd_profile_stop: every GEMM launch is bracketed by CUDA events on the

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libccsd_gb300.so")
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_NOT_CONVERGED, ERR_COMPLEX_ROOT, ERR_DEGENERATE, ERR_NOT_HF, \
     ERR_TIMEOUT = range(10)
 PREC_FP64, PREC_MIXED = 0, 1
+GEMM_FP64, GEMM_SPLIT, GEMM_FP64_TC = 0, 1, 2
 
 
 class Options(ctypes.Structure):
@@ -39,6 +40,7 @@ class Options(ctypes.Structure):
         ("refine", ctypes.c_int),
         ("tol_switch", ctypes.c_double),
         ("autotune", ctypes.c_int),
+        ("fp64_tc", ctypes.c_int),
     ]
 
 
@@ -140,7 +142,10 @@ def _check(h, status):
 def ccsd_default_options(**kw) -> Options:
     opt = Options()
     lib().ccsd_default_options(ctypes.byref(opt))
+    names = {n for n, _ in Options._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown option {k!r}")
         if k == "stream" and v is not None and not isinstance(v, int):
             v = v.cuda_stream  # torch.cuda.Stream
         setattr(opt, k, v)
@@ -228,6 +233,29 @@ def ccsd_stats(h):
     g, gt = ctypes.c_longlong(), ctypes.c_longlong()
     _check(h, lib().ccsd_stats(h, ctypes.byref(f64), ctypes.byref(ftc), ctypes.byref(g), ctypes.byref(gt)))
     return {"flops_fp64": f64.value, "flops_tc": ftc.value, "gemms": g.value, "tc_gemms": gt.value}
+
+
+def ccsd_gemm(form, A, B, C=None, alpha=1.0, beta=0.0, splits=3, reps=1):
+    """C = alpha A B^T + beta C in one arithmetic form (GEMM_FP64, GEMM_SPLIT, GEMM_FP64_TC).
+
+    A (M x K), B (N x K), C (M x N): C-contiguous float64 host arrays; C is allocated when None.
+    Returns (C, ms) with ms the mean device time of one of `reps` repetitions."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("A and B must share K")
+    if C is None:
+        C = np.zeros((M, N))
+    ms = ctypes.c_double()
+    L = lib()
+    L.ccsd_gemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                            _P, _P, ctypes.c_double, _P, ctypes.c_int, _D]
+    L.ccsd_gemm.restype = ctypes.c_int
+    _check(None, L.ccsd_gemm(form, splits, M, N, K, alpha, _ptr(A), _ptr(B), beta, _ptr(C), reps,
+                             ctypes.byref(ms)))
+    return C, ms.value
 
 
 def ccsd_profile_start(h):

@@ -301,6 +301,12 @@ struct PrecScope {
 
 bool refining(ccsd_ctx* c) { return c->opt.precision == CCSD_PREC_MIXED && c->opt.refine; }
 
+// precision of the FP64 evaluations inside a mixed-precision handle (refinement residuals,
+// Hamiltonian-only intermediates, densities): DFMA, or the FP64-grade tensor-core products
+int fp64_prec(ccsd_ctx* c) {
+  return (c->opt.precision == CCSD_PREC_MIXED && c->opt.fp64_tc) ? PREC_FP64_TC : PREC_FP64;
+}
+
 // Solve A x = -rhs by preconditioned Jacobi + DIIS (right transforms); x holds the guess on entry
 int solve_right_linear(ccsd_ctx* c, const double* rhs, double* x, double tol, int maxit) {
   DevBuf res(c->dim), xn(c->dim);
@@ -330,7 +336,7 @@ int solve_left_refined(ccsd_ctx* c, const double* rhs, double* x, double tol) {
   DevBuf rho(c->dim), d(c->dim);
   for (int outer = 0; outer < 20; ++outer) {
     {
-      PrecScope fp64(c, CCSD_PREC_FP64);
+      PrecScope fp64(c, fp64_prec(c));
       left_block(c, x, rho.p, 1);
     }
     launch_axpby(c->dim, 1.0, rhs, 1.0, rho.p, c->st);
@@ -644,7 +650,7 @@ int refine_roots(ccsd_ctx* c, int side, std::vector<double>& w, std::vector<std:
   } catch (const Err& e) {
     if (e.code != CCSD_ERR_NOT_CONVERGED) throw;
   }
-  PrecScope fp64(c, CCSD_PREC_FP64);
+  PrecScope fp64(c, fp64_prec(c));
   const std::vector<double> wm = w;
   std::vector<std::unique_ptr<DevBuf>> fin;
   n += davidson(c, side, nroots, w, fin, c->opt.tol_eom, &vecs, &wm);
@@ -710,7 +716,7 @@ int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol) {
     const double nx = norm(x);
     launch_axpby(dim, 1.0 / nx, x, 0.0, x, c->st);
     {
-      PrecScope fp64(c, CCSD_PREC_FP64);
+      PrecScope fp64(c, fp64_prec(c));
       transform(x, ax.p);
     }
     ++n;
@@ -1128,7 +1134,7 @@ void transition_density(ccsd_ctx* c, int k, int l, double* D) {
 void add_orbital_relaxation(ccsd_ctx* c, int k, int l) {
   const int o = c->o, v = c->v, n = c->n;
   const int64_t nn = (int64_t)n * n, nz = (int64_t)c->naux * nn, m = (int64_t)o * v;
-  PrecScope fp64(c, CCSD_PREC_FP64);
+  PrecScope fp64(c, fp64_prec(c));
   DevBuf Dt(nn);
   transition_density(c, k, l, Dt.p);
   Executor& hx = hf_exec(c);
@@ -1189,7 +1195,7 @@ void compute_densities(ccsd_ctx* c, int k, int l) {
     ex.bind(P.eE, e0.p);
     ex.bind(P.eH, c->Dd.p);
     ex.bind(P.eB, c->Zd.p);
-    PrecScope p(c, refining(c) ? CCSD_PREC_FP64 : ex.precision());
+    PrecScope p(c, refining(c) ? fp64_prec(c) : ex.precision());
     ex.run(P.dens0);
   } else {
     double dw = omega_of(c, l) - omega_of(c, k);
@@ -1203,7 +1209,7 @@ void compute_densities(ccsd_ctx* c, int k, int l) {
     // t-eta = <L_k|tau|R_l> + d^2(g0 E + gamma.Omega)/dt^2 R_l
     launch_tau_expectation(c->vs, r0, left_vec(c, k), Rl, teta.p, c->st);
     {
-      PrecScope p(c, refining(c) ? CCSD_PREC_FP64 : ex.precision());
+      PrecScope p(c, refining(c) ? fp64_prec(c) : ex.precision());
       hess_right(c, g0, gam.p, Rl, hv.p);
     }
     launch_axpby(dim, 1.0, hv.p, 1.0, teta.p, c->st);
@@ -1225,7 +1231,7 @@ void compute_densities(ccsd_ctx* c, int k, int l) {
     ex.bind(P.dR2, const_cast<double*>(Rl) + c->n1);
     ex.bind(P.dH, c->Dd.p);
     ex.bind(P.dB, c->Zd.p);
-    PrecScope p(c, refining(c) ? CCSD_PREC_FP64 : ex.precision());
+    PrecScope p(c, refining(c) ? fp64_prec(c) : ex.precision());
     ex.run(P.dens1);
   }
   sync(c);
@@ -1258,6 +1264,7 @@ void ccsd_default_options(ccsd_options* opt) {
   opt->refine = 1;
   opt->tol_switch = 1e-6;
   opt->autotune = 0;
+  opt->fp64_tc = 1;
 }
 
 const char* ccsd_strerror(ccsd_status s) {
@@ -1367,7 +1374,7 @@ ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int
       // under FP64 refinement the Hamiltonian-only intermediates are built in FP64,
       // so that the refined equations are exactly the FP64 ones
       const int p0 = ex.precision();
-      if (refining(c)) ex.set_precision(CCSD_PREC_FP64, c->opt.splits);
+      if (refining(c)) ex.set_precision(fp64_prec(c), c->opt.splits);
       ex.run(cp.fwd_const);
       ex.set_precision(p0, c->opt.splits);
     }
@@ -1457,7 +1464,7 @@ ccsd_status ccsd_solve_ground(ccsd_handle c, double* e_ccsd, int* iters) {
       for (int outer = 0;; ++outer) {
         if (outer >= 20) throw Err(CCSD_ERR_NOT_CONVERGED, "FP64 refinement of the ground state did not converge");
         {
-          PrecScope fp64(c, CCSD_PREC_FP64);
+          PrecScope fp64(c, fp64_prec(c));
           e = forward(c, c->t.p, om.p);
         }
         ++it;
@@ -1477,7 +1484,7 @@ ccsd_status ccsd_solve_ground(ccsd_handle c, double* e_ccsd, int* iters) {
     DevBuf zero(dim);
     CUDA_OK(cudaMemsetAsync(zero.p, 0, dim * sizeof(double), c->st));
     {
-      PrecScope p(c, refine ? CCSD_PREC_FP64 : c->ex->precision());
+      PrecScope p(c, refine ? fp64_prec(c) : c->ex->precision());
       left_block(c, zero.p, c->eta.p, 1, 1.0);
     }
     launch_precond(c->vs, c->eps.p, c->eta.p, c->lam.p, 0.0, c->st);
@@ -1557,7 +1564,7 @@ ccsd_status ccsd_set_amplitudes(ccsd_handle c, const double* t, const double* la
     DevBuf zero(dim);
     CUDA_OK(cudaMemsetAsync(zero.p, 0, dim * sizeof(double), c->st));
     {
-      PrecScope p(c, refining(c) ? CCSD_PREC_FP64 : c->ex->precision());
+      PrecScope p(c, refining(c) ? fp64_prec(c) : c->ex->precision());
       left_block(c, zero.p, c->eta.p, 1, 1.0);
     }
     if (lambda) {
@@ -2303,6 +2310,81 @@ void expm_device(const std::vector<double>& K, int n, double* U, cudaStream_t st
 }  // namespace
 
 extern "C" {
+
+ccsd_status ccsd_gemm(int form, int splits, int M, int N, int K, double alpha, const double* A, const double* B,
+                      double beta, double* C, int reps, double* ms) {
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C || reps < 1) return CCSD_ERR_ARG;
+  if (form != CCSD_GEMM_FP64 && form != CCSD_GEMM_SPLIT && form != CCSD_GEMM_FP64_TC) return CCSD_ERR_ARG;
+  if (form != CCSD_GEMM_FP64 && beta != 0.0 && beta != 1.0) return CCSD_ERR_ARG;
+  if (form == CCSD_GEMM_SPLIT && splits != 2 && splits != 3) return CCSD_ERR_ARG;
+  return unguarded([&] {
+    const int64_t mk = (int64_t)M * K, nk = (int64_t)N * K, mn = (int64_t)M * N;
+    DevBuf dA(mk), dB(nk), dC(mn), dC0(mn);
+    CUDA_OK(cudaMemcpy(dA.p, A, mk * sizeof(double), cudaMemcpyDefault));
+    CUDA_OK(cudaMemcpy(dB.p, B, nk * sizeof(double), cudaMemcpyDefault));
+    if (beta != 0.0)
+      CUDA_OK(cudaMemcpy(dC0.p, C, mn * sizeof(double), cudaMemcpyDefault));
+    else
+      CUDA_OK(cudaMemset(dC0.p, 0, mn * sizeof(double)));
+    static const Graph empty;
+    cudaStream_t st = nullptr;
+    Executor ex(empty, 1, 1, 1, 1, st);
+    ex.tc_min_flops = 0.0;
+    ex.set_precision(form == CCSD_GEMM_SPLIT ? PREC_MIXED : (form == CCSD_GEMM_FP64_TC ? PREC_FP64_TC : PREC_FP64),
+                     form == CCSD_GEMM_SPLIT ? splits : 3);
+    Strided ga, gb;
+    ga.ndim = gb.ndim = 2;
+    ga.ext[0] = M;
+    gb.ext[0] = N;
+    ga.ext[1] = gb.ext[1] = K;
+    ga.s1[0] = gb.s1[0] = K;
+    ga.s1[1] = gb.s1[1] = 1;
+    ga.s0[0] = ga.s0[1] = gb.s0[0] = gb.s0[1] = 0;
+    cudaEvent_t e0, e1;
+    CUDA_OK(cudaEventCreate(&e0));
+    CUDA_OK(cudaEventCreate(&e1));
+    double total = 0.0;
+    for (int r = 0; r < reps; ++r) {
+      CUDA_OK(cudaMemcpyAsync(dC.p, dC0.p, mn * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      CUDA_OK(cudaEventRecord(e0, st));
+      if (form == CCSD_GEMM_FP64) {
+        GemmArgs g;
+        g.batch = 1;
+        g.M = M;
+        g.N = N;
+        g.K = K;
+        g.A = dA.p;
+        g.sAb = 0;
+        g.sAm = K;
+        g.sAk = 1;
+        g.B = dB.p;
+        g.sBb = 0;
+        g.sBn = K;
+        g.sBk = 1;
+        g.C = dC.p;
+        g.sCb = 0;
+        g.sCm = N;
+        g.sCn = 1;
+        g.alpha = alpha;
+        g.beta = beta;
+        launch_dgemm(g, st);
+      } else if (!ex.tc_contract(M, N, K, dA.p, ga, dB.p, gb, dC.p, N, 1, alpha, beta, false, false)) {
+        throw Err(CCSD_ERR_ARG, "contraction shape not supported by the tensor-core path");
+      }
+      CUDA_OK(cudaEventRecord(e1, st));
+      CUDA_OK(cudaEventSynchronize(e1));
+      float t = 0.f;
+      CUDA_OK(cudaEventElapsedTime(&t, e0, e1));
+      total += t;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ex.tc_error()) throw Err(CCSD_ERR_TIMEOUT, "a tensor-core kernel wait timed out");
+    CUDA_OK(cudaGetLastError());
+    CUDA_OK(cudaMemcpy(C, dC.p, mn * sizeof(double), cudaMemcpyDefault));
+    if (ms) *ms = total / reps;
+  });
+}
 
 ccsd_status ccsd_scf(const double* eps, const double* h, const double* B, int o, int v, int naux, double tol,
                      double* U_out, double* h_out, double* B_out, int* iters) {

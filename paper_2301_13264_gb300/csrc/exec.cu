@@ -262,7 +262,7 @@ void Executor::exec_contract(const Op& op) {
 
   // tensor-core path: operands are gathered straight from their strided FP64
   // layout into bf16 slices (no FP64 staging copy)
-  if (prec_ == PREC_MIXED && flops >= tc_min_flops && Bt == 1) {
+  if ((prec_ == PREC_MIXED || prec_ == PREC_FP64_TC) && flops >= tc_min_flops && Bt == 1) {
     auto gather = [&](std::map<char, std::pair<int64_t, int64_t>>& es, const std::vector<char>& rows) {
       Strided g;
       std::vector<char> order = rows;

@@ -23,7 +23,9 @@
 
 namespace ccsd {
 
-enum Precision : int { PREC_FP64 = 0, PREC_MIXED = 1 };
+// PREC_FP64_TC: FP64-grade contractions on the tensor cores (fixed-point bf16 slices,
+// exact per-chunk sums; fp64_tc.cu) for contractions above tc_min_flops, FP64 DFMA below
+enum Precision : int { PREC_FP64 = 0, PREC_MIXED = 1, PREC_FP64_TC = 2 };
 
 struct ExecStats {
   int64_t gemm_calls = 0, tc_calls = 0, packs = 0, scatters = 0, axpys = 0, ladders = 0;
@@ -125,6 +127,11 @@ class Executor {
   bool tc_contract(int M, int N, int K, const double* A, const Strided& Ag, const double* B, const Strided& Bg,
                    double* C, int64_t sCm, int64_t sCn, double alpha, double beta, bool a_const, bool b_const,
                    const Strided* om = nullptr, const Strided* on = nullptr);
+  // the same contraction through the FP64-grade tensor-core products (fp64_tc.cu);
+  // constant operands keep their fixed-point slices cached like the split slices
+  bool fp64tc_contract(int M, int N, int K, const double* A, const Strided& Ag, const double* B, const Strided& Bg,
+                       double* C, int64_t sCm, int64_t sCn, double alpha, double beta, bool a_const, bool b_const,
+                       const Strided* om = nullptr, const Strided* on = nullptr);
   // tcgen05 GEMM on prepared bf16 slices: a [S][Mp][Kp], b [S][Np][Kp] (rows and K
   // zero-padded; Mp a multiple of 128, Np of the tile width chosen for N);
   // C[m*sCm + n*sCn] = alpha * sum + beta * C.

@@ -309,6 +309,7 @@ bool Executor::try_ladder(const Op& op) {
   }
   const double flops_each = 2.0 * (double)nrows * np * np;
   const bool mixed = (prec_ == PREC_MIXED && flops_each >= tc_min_flops);
+  const bool fp64tc = (prec_ == PREC_FP64_TC && flops_each >= tc_min_flops);
   const int2* pairs = pair_table();
   const double* Wp = ts_[ladder_w_].p;
   // row tables of the pair-symmetric form: device copies kept for the executor's
@@ -466,13 +467,31 @@ bool Executor::try_ladder(const Op& op) {
       g.beta = 0.0;
       ProfRec r{};
       prof_begin(r);
-      launch_dgemm(g, st_);
-      prof_end(r, false);
+      if (fp64tc) {
+        // FP64-grade tensor-core products; the fixed-point slices of W+- stay cached
+        Strided ga, gw;
+        ga.ndim = gw.ndim = 2;
+        ga.ext[0] = nrows;
+        gw.ext[0] = np;
+        ga.ext[1] = gw.ext[1] = np;
+        ga.s1[0] = gw.s1[0] = np;
+        ga.s1[1] = gw.s1[1] = 1;
+        ga.s0[0] = ga.s0[1] = gw.s0[0] = gw.s0[1] = 0;
+        fp64tc_contract((int)nrows, np, np, g.A, ga, g.B, gw, g.C, np, 1, 1.0, 0.0, false, true);
+      } else {
+        launch_dgemm(g, st_);
+      }
+      prof_end(r, fp64tc);
     }
     tmp_free(ap);
     tmp_free(am);
-    stats.gemm_calls += 2;
-    stats.gemm_flops += 2 * flops_each;
+    if (fp64tc) {
+      stats.tc_calls += 2;
+      stats.tc_flops += 2 * flops_each;
+    } else {
+      stats.gemm_calls += 2;
+      stats.gemm_flops += 2 * flops_each;
+    }
   }
   count_launches(1);
   if (sym)

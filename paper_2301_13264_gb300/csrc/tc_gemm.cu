@@ -32,6 +32,7 @@
 #include <utility>
 
 #include "exec.h"
+#include "fp64_tc.h"
 #include "tcgen05.cuh"
 
 namespace ccsd {
@@ -278,7 +279,7 @@ static EncodeTiled encoder() {
   return fn;
 }
 
-static CUtensorMap make_map(const void* base, int64_t rows, int64_t Kp, int S, int box_rows) {
+CUtensorMap make_map(const void* base, int64_t rows, int64_t Kp, int S, int box_rows) {
   CUtensorMap m;
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)S};
   cuuint64_t strides[2] = {(cuuint64_t)(Kp * 2), (cuuint64_t)(rows * Kp * 2)};
@@ -399,6 +400,7 @@ static void launch_tc(dim3 grid, const CUtensorMap& ta, const CUtensorMap& tb, c
 bool Executor::tc_contract(int M, int N, int K, const double* A, const Strided& Ag, const double* B,
                            const Strided& Bg, double* C, int64_t sCm, int64_t sCn, double alpha, double beta,
                            bool a_const, bool b_const, const Strided* om, const Strided* on) {
+  if (prec_ == PREC_FP64_TC) return fp64tc_contract(M, N, K, A, Ag, B, Bg, C, sCm, sCn, alpha, beta, a_const, b_const, om, on);
   if (M < 1 || N < 1 || K < 1) return false;
   if (beta != 0.0 && beta != 1.0) return false;
   Strided ag = Ag, bg = Bg;
@@ -443,6 +445,57 @@ bool Executor::tc_contract(int M, int N, int K, const double* A, const Strided& 
   __nv_bfloat16* a = get(A, ag, M, Mp, a_const, ownA);
   __nv_bfloat16* b = get(B, bg, N, Np, b_const, ownB);
   tc_run(a, Mp, b, Np, K, Kp, S, M, N, C, sCm, sCn, alpha, beta, om, on, BN, ch.nsplit);
+  if (ownA) cudaFreeAsync(a, st_);
+  if (ownB) cudaFreeAsync(b, st_);
+  return true;
+}
+
+bool Executor::fp64tc_contract(int M, int N, int K, const double* A, const Strided& Ag, const double* B,
+                               const Strided& Bg, double* C, int64_t sCm, int64_t sCn, double alpha, double beta,
+                               bool a_const, bool b_const, const Strided* om, const Strided* on) {
+  if (M < 1 || N < 1 || K < 1) return false;
+  if (beta != 0.0 && beta != 1.0) return false;
+  Strided ag = Ag, bg = Bg;
+  if (M < tc::BM && N > M) {
+    std::swap(M, N);
+    std::swap(A, B);
+    std::swap(ag, bg);
+    std::swap(a_const, b_const);
+    std::swap(sCm, sCn);
+    std::swap(om, on);
+  }
+  const int64_t Kp = ((int64_t)K + tc::BK - 1) / tc::BK * tc::BK;
+  const int64_t Mp = ((int64_t)M + tc::BM - 1) / tc::BM * tc::BM;
+  const int64_t Np = ((int64_t)N + oz::BN - 1) / oz::BN * oz::BN;
+  if (Np / oz::BN > 65535) return false;
+  if (!tc_err_) {
+    if (cudaMalloc(&tc_err_, sizeof(int)) != cudaSuccess) throw std::runtime_error("tc flag allocation failed");
+    cudaMemsetAsync(tc_err_, 0, sizeof(int), st_);
+  }
+  auto get = [&](const double* src, const Strided& g, int64_t rows, int64_t rows_p, bool cst, bool& owned) {
+    if (cst) {
+      for (CacheEntry* e : cache_)
+        if (e->src == src && same_gather(e->g, g) && e->rows_p == rows_p && e->K == K && e->S == oz::S) {
+          owned = false;
+          return e->dev;
+        }
+    }
+    const size_t bytes = oz::operand_bytes(rows_p, Kp);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, st_) != cudaSuccess) throw std::runtime_error("tc operand allocation failed");
+    oz::pack(st_, src, g, rows, rows_p, K, Kp, p);
+    owned = !cst;
+    if (cst) {
+      CacheEntry* e = new CacheEntry{src, g, rows_p, (int64_t)K, oz::S, p, bytes};
+      cache_.push_back(e);
+      cache_bytes_ += e->bytes;
+    }
+    return p;
+  };
+  bool ownA = false, ownB = false;
+  void* a = get(A, ag, M, Mp, a_const, ownA);
+  void* b = get(B, bg, N, Np, b_const, ownB);
+  last_tc_issued = oz::gemm(st_, a, Mp, b, Np, Kp, M, N, C, sCm, sCn, alpha, beta, om, on, 0, tc_err_);
   if (ownA) cudaFreeAsync(a, st_);
   if (ownB) cudaFreeAsync(b, st_);
   return true;
@@ -584,6 +637,20 @@ void Executor::tc_run(const void* a, int64_t Mp, const void* b, int64_t Np, int 
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw std::runtime_error(std::string("tc gemm launch: ") + cudaGetErrorString(e));
+}
+
+void launch_split_reduce_fp64(int M, int N, int nsplit, const double* part, double* C, long long sCm, long long sCn,
+                              int beta_zero, const Strided* om, const Strided* on, cudaStream_t st) {
+  const long long tot = (long long)M * N;
+  Strided gm, gn;
+  gm.ndim = gn.ndim = 0;
+  if (om && on) {
+    gm = *om;
+    gn = *on;
+  }
+  count_launches(1);
+  tc::k_tc_reduce<<<(int)std::min<long long>((tot + 255) / 256, 152 * 16), 256, 0, st>>>(
+      M, N, nsplit, part, C, sCm, sCn, beta_zero, (om && on) ? 1 : 0, gm, gn);
 }
 
 }  // namespace ccsd

@@ -106,5 +106,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 3-D TMA map over bf16 slices [S][rows][Kp]: boxes of 64 K x box_rows rows x 1 slice,
+// 128-byte swizzle (tc_gemm.cu)
+CUtensorMap make_map(const void* base, int64_t rows, int64_t Kp, int S, int box_rows);
+
 }  // namespace tc
 }  // namespace ccsd
