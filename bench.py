@@ -44,12 +44,13 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="thymine_adz")
     ap.add_argument("--nvec", type=int, default=8)
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--precision", choices=["mixed", "fp64", "fp64tc"], default="mixed")
     ap.add_argument("--splits", type=int, default=3)
     ap.add_argument("--amplitudes", choices=["solve", "synthetic"], default="solve",
                     help="converge the ground state in set-up, or use seeded synthetic amplitudes")
-    ap.add_argument("--ttc", choices=["mixed", "fp64", "both"], default=None,
-                    help="instead of transform throughput, time create -> ground -> EOM (2 roots) -> couplings")
+    ap.add_argument("--ttc", default=None,
+                    help="instead of transform throughput, time create -> ground -> EOM (2 roots) -> couplings "
+                         "for the comma-separated forms among mixed, fp64, fp64tc ('both' = mixed,fp64)")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of the single-system bench, time batched transforms of this many small systems")
     ap.add_argument("--no-autotune", action="store_true", help="batch mode: tile widths from the output width")
@@ -235,7 +236,7 @@ def run_ours(args, rank, world, local_rank):
     o, v, naux = H.o, H.v, H.naux
     dim = B.vector_dim(o, v)
     stream = torch.cuda.Stream()
-    prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_FP64
+    prec = precision_of(args.precision)
     opt = B.ccsd_default_options(precision=prec, splits=args.splits, stream=stream, tol_res=1e-7, tol_lin=1e-6,
                                  max_iter=100)
     h = B.ccsd_create(H.eps, H.h, H.B, o, v, naux, opt)
@@ -321,14 +322,18 @@ def run_ours(args, rank, world, local_rank):
     executed = prof["ladder_flops"] / n_ladder / (lad_ms * 1e-3) / 1e12 if lad_ms > 0 else 0.0
     # the split arithmetic issues nprod bf16 products per FP64-equivalent multiply-add,
     # so its peak is the bf16 peak / nprod (FP64 DFMA path: the FP64 peak)
-    nprod = (3 if args.splits == 2 else 6) if prec == B.PREC_MIXED else 1
-    peak_split = peak / nprod if prec == B.PREC_MIXED else FP64_PEAK_TFLOPS
+    # (FP64-grade tensor-core products: 28; FP64 DFMA path: the FP64 peak)
+    tensor = prec != B.PREC_FP64
+    nprod = {B.PREC_MIXED: 3 if args.splits == 2 else 6, B.PREC_FP64_TC: 28}.get(prec, 1)
+    peak_split = peak / nprod if tensor else FP64_PEAK_TFLOPS
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak_split, "unit": "TFLOP/s",
                 "frac": achieved / peak_split, "traffic": LADDER_TRAFFIC.get((args.workload, args.nvec, nprod)),
-                "kernel": "k_tc_gemm<256> (pp-ladder, +/- GEMM pair)",
+                "kernel": ("k_tc_gemm<256>" if prec == B.PREC_MIXED else
+                           "k_tc_dgemm" if tensor else "k_dgemm") + " (pp-ladder, +/- GEMM pair)",
                 "peak_source": (f"bf16_tflops_sustained of {src} MEASURED_PEAKS.json / {nprod} bf16 products per "
-                                "FP64-equivalent multiply-add (split-bf16 arithmetic)") if prec == B.PREC_MIXED
-                else "FP64 DFMA peak: 152 SMs x 2.07 GHz x 4 flop/clk",
+                                "FP64-equivalent multiply-add (" +
+                                ("split-bf16" if prec == B.PREC_MIXED else "fixed-point slice") + " arithmetic)")
+                if tensor else "FP64 DFMA peak: 152 SMs x 2.07 GHz x 4 flop/clk",
                 "peak_bf16": peak, "frac_of_bf16_peak": achieved / peak,
                 "algorithmic_flops_per_launch": ladder_alg,
                 "algorithmic_definition": "o^2 v^4 / 4 multiply-adds per vector (pair-packed ladder) x nvec",
@@ -343,8 +348,7 @@ def run_ours(args, rank, world, local_rank):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None,
-           "dtype": "f64 (bf16x%d split tensor-core products, fp32 accumulate)" % (3 if args.splits == 2 else 6)
-           if prec == B.PREC_MIXED else "f64",
+           "dtype": DTYPE[prec] % nprod,
            "data": "synthetic",
            "config": {"workload": f"{args.workload} o={o} v={v} naux={naux}", "nvec": args.nvec,
                       "step": f"right + left block transform of {args.nvec} vectors",
@@ -362,6 +366,16 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(out), flush=True)
 
 
+def precision_of(name):
+    """The library's precision constant for a form name (mixed, fp64, fp64tc)."""
+    from paper_2301_13264_gb300 import binding as B
+    return {"mixed": B.PREC_MIXED, "fp64": B.PREC_FP64, "fp64tc": B.PREC_FP64_TC}[name]
+
+
+DTYPE = {0: "f64", 1: "f64 (bf16x%d split tensor-core products, fp32 accumulate)",
+         2: "f64 (FP64-grade tensor-core products: 7 fixed-point bf16 slices, %d products, exact chunk sums)"}
+
+
 def run_ttc(args):
     """Time-to-converged coupling: wall time from ccsd_create through the
     derivative couplings F_12, F_01, F_20 along (h1, B1), per precision form, at
@@ -371,12 +385,15 @@ def run_ttc(args):
     from paper_2301_13264_gb300.synth import workload
 
     H = workload(args.workload)
-    forms = ["mixed", "fp64"] if args.ttc == "both" else [args.ttc]
+    forms = ["mixed", "fp64"] if args.ttc == "both" else args.ttc.split(",")
+    for f in forms:
+        if f not in ("mixed", "fp64", "fp64tc"):
+            raise SystemExit(f"unknown form {f!r}")
     out = {"metric": "time-to-converged coupling", "unit": "s", "higher_is_better": False,
            "workload": f"{args.workload} o={H.o} v={H.v} naux={H.naux}", "pairs": [[1, 2], [0, 1], [2, 0]],
            "forms": {}}
     for form in forms:
-        prec = B.PREC_MIXED if form == "mixed" else B.PREC_FP64
+        prec = precision_of(form)
         opt = B.ccsd_default_options(precision=prec, splits=args.splits, tol_res=1e-10, tol_eom=1e-8,
                                      tol_lin=1e-9, max_iter=200, refine=1)
         torch.cuda.synchronize()
@@ -397,12 +414,14 @@ def run_ttc(args):
                               "e_ccsd": e, "omega": w, "F": F, "iters": [it_g, it_r, it_l],
                               "stats": B.ccsd_stats(h)}
         B.ccsd_destroy(h)
-    if len(forms) == 2:
-        m, f = out["forms"]["mixed"], out["forms"]["fp64"]
-        out["speedup"] = f["seconds"] / m["seconds"]
-        out["energy_diff"] = abs(m["e_ccsd"] - f["e_ccsd"])
-        out["omega_diff"] = max(abs(a - b) for a, b in zip(m["omega"], f["omega"]))
-        out["coupling_rel_diff"] = max(abs(a - b) / abs(b) for a, b in zip(m["F"], f["F"]))
+    if "fp64" in out["forms"]:
+        f = out["forms"]["fp64"]
+        for name, m in out["forms"].items():
+            if name == "fp64":
+                continue
+            m["vs_fp64"] = {"speedup": f["seconds"] / m["seconds"], "energy_diff": abs(m["e_ccsd"] - f["e_ccsd"]),
+                            "omega_diff": max(abs(a - b) for a, b in zip(m["omega"], f["omega"])),
+                            "coupling_rel_diff": max(abs(a - b) / abs(b) for a, b in zip(m["F"], f["F"]))}
     print(json.dumps(out), flush=True)
 
 
@@ -423,7 +442,7 @@ def run_batch(args):
 
     shapes = batch_shapes(args.batch)
     nvec = args.nvec
-    prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_FP64
+    prec = precision_of(args.precision)
     hs, X, Y = [], [], []
     t0 = time.perf_counter()
     for k, (o, v, naux) in enumerate(shapes):
@@ -500,7 +519,7 @@ def run_batch_eom(args):
 
     shapes = batch_shapes(args.batch)
     nroots = args.batch_eom
-    prec = B.PREC_MIXED if args.precision == "mixed" else B.PREC_FP64
+    prec = precision_of(args.precision)
     hs = []
     t0 = time.perf_counter()
     for k, (o, v, naux) in enumerate(shapes):

@@ -58,11 +58,16 @@ typedef enum {
   CCSD_ERR_TIMEOUT = 9        /* a device-side wait exceeded its budget */
 } ccsd_status;
 
-enum { CCSD_PREC_FP64 = 0, CCSD_PREC_MIXED = 1 };
+/* CCSD_PREC_FP64: every contraction in FP64 (DFMA).
+ * CCSD_PREC_MIXED: contractions above tc_min_flops as split-bf16 tensor-core products (FP32
+ *   accumulation), optionally refined to the FP64 tolerances (refine, fp64_tc).
+ * CCSD_PREC_FP64_TC: contractions above tc_min_flops as FP64-grade tensor-core products (see
+ *   fp64_tc below); the solvers run directly to the FP64 tolerances, without refinement. */
+enum { CCSD_PREC_FP64 = 0, CCSD_PREC_MIXED = 1, CCSD_PREC_FP64_TC = 2 };
 enum { CCSD_GUESS_MP2 = 0 };
 
 typedef struct {
-  int precision;        /* CCSD_PREC_FP64 or CCSD_PREC_MIXED (tensor-core split products) */
+  int precision;        /* CCSD_PREC_FP64, CCSD_PREC_MIXED or CCSD_PREC_FP64_TC; anything else: CCSD_ERR_ARG */
   int splits;           /* mixed mode: bf16 slices per FP64 operand (2 or 3) */
   int relax_orbitals;   /* 0: orbitals fixed and x-independent (unrelaxed coupling); 1: Hartree-Fock
                            orbitals that follow x (Eq. orbitalrelax): the inputs must be Hartree-Fock

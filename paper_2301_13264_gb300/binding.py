@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libccsd_gb300.so")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_NOT_CONVERGED, ERR_COMPLEX_ROOT, ERR_DEGENERATE, ERR_NOT_HF, \
     ERR_TIMEOUT = range(10)
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_FP64_TC = 0, 1, 2
 GEMM_FP64, GEMM_SPLIT, GEMM_FP64_TC = 0, 1, 2
 
 

@@ -304,6 +304,7 @@ bool refining(ccsd_ctx* c) { return c->opt.precision == CCSD_PREC_MIXED && c->op
 // precision of the FP64 evaluations inside a mixed-precision handle (refinement residuals,
 // Hamiltonian-only intermediates, densities): DFMA, or the FP64-grade tensor-core products
 int fp64_prec(ccsd_ctx* c) {
+  if (c->opt.precision == CCSD_PREC_FP64_TC) return PREC_FP64_TC;
   return (c->opt.precision == CCSD_PREC_MIXED && c->opt.fp64_tc) ? PREC_FP64_TC : PREC_FP64;
 }
 
@@ -644,11 +645,16 @@ bool verbose_solvers() {
 int refine_roots(ccsd_ctx* c, int side, std::vector<double>& w, std::vector<std::unique_ptr<DevBuf>>& vecs) {
   const int nroots = (int)w.size();
   int n = 0;
-  try {
-    for (int k = 0; k < nroots; ++k) n += refine_eigenpair(c, side, vecs[k]->p, w[k], c->opt.tol_eom);
-    return n;
-  } catch (const Err& e) {
-    if (e.code != CCSD_ERR_NOT_CONVERGED) throw;
+  // With FP64-grade tensor-core transforms an FP64 transform costs a few mixed ones, and a
+  // Davidson continuation of all roots at once (one block transform per iteration) is
+  // cheaper than per-root correction equations solved with single-vector transforms.
+  if (fp64_prec(c) != PREC_FP64_TC) {
+    try {
+      for (int k = 0; k < nroots; ++k) n += refine_eigenpair(c, side, vecs[k]->p, w[k], c->opt.tol_eom);
+      return n;
+    } catch (const Err& e) {
+      if (e.code != CCSD_ERR_NOT_CONVERGED) throw;
+    }
   }
   PrecScope fp64(c, fp64_prec(c));
   const std::vector<double> wm = w;
@@ -1299,7 +1305,9 @@ ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int
     c->opt = *opt;
   else
     ccsd_default_options(&c->opt);
-  if (c->opt.relax_orbitals != 0 && c->opt.relax_orbitals != 1) {
+  if ((c->opt.relax_orbitals != 0 && c->opt.relax_orbitals != 1) ||
+      (c->opt.precision != CCSD_PREC_FP64 && c->opt.precision != CCSD_PREC_MIXED &&
+       c->opt.precision != CCSD_PREC_FP64_TC)) {
     delete c;
     return CCSD_ERR_ARG;
   }

@@ -1,4 +1,5 @@
-"""FP64-grade tensor-core products (fixed-point bf16 slices, exact chunk sums) against FP64.
+"""FP64-grade tensor-core products (fixed-point bf16 slices, exact chunk sums) against FP64,
+as plain GEMMs and as the handle form CCSD_PREC_FP64_TC against the oracle.
 
 The reference is the plain definition C = alpha A B^T + beta C evaluated by numpy in
 FP64.  The scheme keeps 49 bits of every operand below its row's leading bit and drops
@@ -79,3 +80,82 @@ def test_throughput_against_dfma():
     print(f"ladder-shaped GEMM {M}x{N}x{K}: FP64-grade tensor cores {ms_tc:.2f} ms ({tf_tc:.1f} TFLOP/s incl. "
           f"slicing), FP64 DFMA {ms_64:.2f} ms ({tf_64:.2f} TFLOP/s)")
     assert ms_tc < ms_64
+
+
+def _fp64tc_handle(H, **kw):
+    o = dict(precision=B.PREC_FP64_TC, tc_min_flops=0.0)
+    o.update(kw)
+    return B.ccsd_create(H.eps, H.h, H.B, H.o, H.v, H.naux, B.ccsd_default_options(**o))
+
+
+@pytest.mark.parametrize("o,v,naux", [(6, 48, 60), (9, 37, 41)])
+def test_fp64tc_residual_and_transforms_match_oracle(o, v, naux):
+    """Handle form CCSD_PREC_FP64_TC with every contraction on the tensor cores: residual,
+    energy and right/left transforms within 1e-11 of the oracle relative to the largest
+    element, the bound of the FP64 form (the split-bf16 form is at 2e-5 here)."""
+    from oracle import ccsd as cc
+    from oracle.solvers import System, Vec
+    from paper_2301_13264_gb300.synth import make_hamiltonian, random_amplitudes
+
+    H = make_hamiltonian(o, v, naux, seed=4)
+    X1, X2 = random_amplitudes(o, v, 8, scale=0.03, nvec=4)
+    flat = lambda a, b: np.concatenate([np.asarray(a).reshape(-1), np.asarray(b).reshape(-1)])  # noqa: E731
+    relerr = lambda a, b: np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max()  # noqa: E731
+    t = flat(X1[0], X2[0])
+    h = _fp64tc_handle(H)
+    try:
+        om = np.zeros_like(t)
+        e = B.ccsd_residual(h, t, om)
+        assert B.ccsd_stats(h)["tc_gemms"] > 0, "tensor-core path not taken"
+        B.ccsd_set_amplitudes(h, t, np.zeros_like(t))
+        X = np.stack([flat(X1[k], X2[k]) for k in (1, 2, 3)])
+        YR, YL = np.zeros_like(X), np.zeros_like(X)
+        B.ccsd_jacobian_transform(h, 0, 3, X, YR)
+        B.ccsd_jacobian_transform(h, 1, 3, X, YL)
+    finally:
+        B.ccsd_destroy(h)
+    c1, c2, ce = cc.residual(cc.as_t(X1[0]), cc.as_t(X2[0]), cc.as_t(H.h), cc.as_t(H.B), o)
+    assert relerr(om, flat(c1, c2)) < 1e-11
+    assert abs(e - float(ce)) < 1e-11 * abs(float(ce))
+    S_ = System(H.eps, H.h, H.B, o)
+    tv = Vec(cc.as_t(X1[0]), cc.as_t(X2[0]))
+    for k in range(3):
+        r = Vec(cc.as_t(X1[k + 1]), cc.as_t(X2[k + 1]))
+        ar, la = S_.right(tv, r), S_.left(tv, r)
+        assert relerr(YR[k], flat(ar.x1, ar.x2)) < 1e-11
+        assert relerr(YL[k], flat(la.x1, la.x2)) < 1e-11
+
+
+def test_fp64tc_pipeline_meets_fp64_tolerances():
+    """The whole pipeline in the FP64-grade tensor-core form, solved directly to the FP64
+    tolerances: energy within 1e-9 Eh of the oracle, excitation energies within 1e-8,
+    couplings within 1e-7 relative."""
+    from oracle.solvers import System
+    from paper_2301_13264_gb300.synth import workload
+
+    H = workload("small")
+    S_ = System(H.eps, H.h, H.B, H.o)
+    res = S_.run(2, tol=1e-12, tol_eom=1e-10, tol_lin=1e-12)
+    h = _fp64tc_handle(H, tol_res=1e-11, tol_eom=1e-9, tol_lin=1e-11, max_iter=200)
+    try:
+        e, _ = B.ccsd_solve_ground(h)
+        w, _ = B.eom_solve_right(h, 2)
+        B.eom_solve_left(h, 2)
+        F = {kl: B.ccsd_derivative_coupling(h, kl[0], kl[1], 1, H.h1, H.B1)[0] for kl in [(1, 2), (0, 1), (2, 0)]}
+        assert B.ccsd_stats(h)["tc_gemms"] > 0
+    finally:
+        B.ccsd_destroy(h)
+    assert abs(e - res.e_ccsd) < 1e-9
+    assert np.abs(np.array(w) - np.array(res.omega)).max() < 1e-8
+    for (k, l), f in F.items():
+        ref = S_.coupling(res, k, l, H.h1, H.B1, tol_lin=1e-12)
+        assert abs(f - ref) < 1e-7 * abs(ref)
+
+
+def test_unknown_precision_is_rejected():
+    from paper_2301_13264_gb300.synth import make_hamiltonian
+
+    H = make_hamiltonian(2, 4, 6, seed=1)
+    with pytest.raises(B.CCSDError) as e:
+        B.ccsd_create(H.eps, H.h, H.B, H.o, H.v, H.naux, B.ccsd_default_options(precision=3))
+    assert e.value.status == B.ERR_ARG
