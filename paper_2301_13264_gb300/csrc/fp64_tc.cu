@@ -30,7 +30,8 @@
 // the 7 slices of the B tile into one of 2 B-group buffers and the A slices one by
 // one into a 4-stage ring (TMA, 3-D maps whose third coordinate is the slice);
 // warp 1 lane 0 issues, for each A slice s, the products with B slices t <= 6 - s
-// into the level-(s+t) accumulator (tcgen05.mma kind::f16, 128 x 64 x 16), and
+// into the level-(s+t) accumulators (tcgen05.mma kind::f16, 128 x 64nt x 16: up to four
+// B slices, adjacent in shared memory, against adjacent level accumulators), and
 // after the last K tile of a chunk commits to the read-out barrier; warps 2..9
 // (TMEM lane quarter = warp mod 4, one half of the columns each) read the seven
 // accumulators, release them to the MMA warp and, after the last chunk, write
@@ -90,6 +91,12 @@ __device__ __forceinline__ long long dim_off(long long x, const Strided& g) {
     x /= e;
   }
   return off;
+}
+
+// kind::f16 instruction descriptor (FP32 accumulator, bf16 A and B, K-major) for M = 128 and
+// N = n (a multiple of 16 up to 256)
+__device__ __forceinline__ uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -247,12 +254,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           tc::fence_after();
           const uint32_t a0 = sA0 + as * A_BYTES;
-          for (int t = 0; s + t < S; ++t) {
-            const uint32_t b0 = sB0 + bs * BG_BYTES + t * B_BYTES;
-            const uint32_t d = tmem + (uint32_t)((s + t) * BN);
+          // The products a_s b_t, t = 0 .. 6-s, land in the levels s .. 6, whose accumulators are
+          // contiguous in TMEM, and the B slices t are contiguous 64-row tiles in the B group: up
+          // to four of them form one B operand of N = 64 nt rows, so one MMA covers nt products.
+          for (int t0 = 0; t0 < S - s; t0 += 4) {
+            const int nt = min(4, S - s - t0);
+            const uint32_t b0 = sB0 + bs * BG_BYTES + t0 * B_BYTES;
+            const uint32_t d = tmem + (uint32_t)((s + t0) * BN);
+            const uint32_t idsc = idesc_n(BN * nt);
 #pragma unroll
             for (int j = 0; j < BK / 16; ++j)
-              tc::mma_bf16(d, tc::smem_desc(a0 + 32 * j), tc::smem_desc(b0 + 32 * j), tc::idesc<BN>(),
+              tc::mma_bf16(d, tc::smem_desc(a0 + 32 * j), tc::smem_desc(b0 + 32 * j), idsc,
                            (kc == 0 && s == 0 && j == 0) ? 0u : 1u);
           }
           tc::mma_commit(aempty + 8 * as);
