@@ -645,16 +645,11 @@ bool verbose_solvers() {
 int refine_roots(ccsd_ctx* c, int side, std::vector<double>& w, std::vector<std::unique_ptr<DevBuf>>& vecs) {
   const int nroots = (int)w.size();
   int n = 0;
-  // With FP64-grade tensor-core transforms an FP64 transform costs a few mixed ones, and a
-  // Davidson continuation of all roots at once (one block transform per iteration) is
-  // cheaper than per-root correction equations solved with single-vector transforms.
-  if (fp64_prec(c) != PREC_FP64_TC) {
-    try {
-      for (int k = 0; k < nroots; ++k) n += refine_eigenpair(c, side, vecs[k]->p, w[k], c->opt.tol_eom);
-      return n;
-    } catch (const Err& e) {
-      if (e.code != CCSD_ERR_NOT_CONVERGED) throw;
-    }
+  try {
+    for (int k = 0; k < nroots; ++k) n += refine_eigenpair(c, side, vecs[k]->p, w[k], c->opt.tol_eom);
+    return n;
+  } catch (const Err& e) {
+    if (e.code != CCSD_ERR_NOT_CONVERGED) throw;
   }
   PrecScope fp64(c, fp64_prec(c));
   const std::vector<double> wm = w;
@@ -700,7 +695,7 @@ int davidson_refined(ccsd_ctx* c, int side, int nroots, std::vector<double>& w,
 // For a root above the lowest, (A - w) is indefinite on the complement of x (the lower
 // roots give negative eigenvalues), which GMRES handles; each outer step gains the
 // mixed operator's accuracy, so two or three FP64 transforms per root replace an FP64
-// Davidson continuation.  Returns the transforms used; throws if |r| stops decreasing.
+// Davidson continuation.  Returns the transforms used; throws if an outer step gains less than 10x.
 int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol) {
   const int64_t dim = c->dim;
   constexpr int KR = 16;  // Krylov vectors per restart
@@ -733,7 +728,9 @@ int refine_eigenpair(ccsd_ctx* c, int side, double* x, double& w, double tol) {
     if (verbose_solvers())
       fprintf(stderr, "[refine side %d] outer %d: w = %.12f, |r| = %.3e (%d transforms so far)\n", side, outer, w, rn, n);
     if (rn < tol) return n;
-    if (!(rn < 0.5 * last)) throw Err(CCSD_ERR_NOT_CONVERGED, "eigenpair refinement stalled");
+    // an outer step that gains less than a factor 10 means the correction equation is
+    // hard for GMRES (a nearby root): the Davidson continuation is cheaper from here
+    if (!(rn < 0.1 * last)) throw Err(CCSD_ERR_NOT_CONVERGED, "eigenpair refinement stalled");
     last = rn;
     // GMRES on Op(v) = P (A - w) P M^-1 v, Op(q) = -r, d = P M^-1 q (q accumulated in u)
     auto op = [&](const double* v, double* out) {
