@@ -1,5 +1,9 @@
 // FP64-grade contraction on the tensor cores, for the FP64 residuals of the
-// refined mixed-precision solves.
+// refined mixed-precision solves.  The operand splitting follows the error-free
+// transformation of matrix products of Ozaki, Ogita, Oishi and Rump (Numer.
+// Algorithms 59, 2012: fixed-point slices whose partial products are exact),
+// adapted here to bf16 operands with FP32 TMEM accumulation: exactness comes from
+// bounding each accumulator's sum per K chunk, not from integer arithmetic.
 //
 // Operand layout.  An FP64 operand X (rows x K) is scaled row by row by 2^-e_r,
 // with e_r the smallest exponent such that every |X_rk| < 2^e_r, and cut into
