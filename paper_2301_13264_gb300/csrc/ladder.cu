@@ -477,7 +477,8 @@ bool Executor::try_ladder(const Op& op) {
         ga.s1[0] = gw.s1[0] = np;
         ga.s1[1] = gw.s1[1] = 1;
         ga.s0[0] = ga.s0[1] = gw.s0[0] = gw.s0[1] = 0;
-        fp64tc_contract((int)nrows, np, np, g.A, ga, g.B, gw, g.C, np, 1, 1.0, 0.0, false, true);
+        if (!fp64tc_contract((int)nrows, np, np, g.A, ga, g.B, gw, g.C, np, 1, 1.0, 0.0, false, true))
+          launch_dgemm(g, st_);
       } else {
         launch_dgemm(g, st_);
       }
