@@ -262,8 +262,9 @@ void ccsd_batch_destroy(ccsd_batch b);
 ccsd_status ccsd_derivative_coupling_noalloc(ccsd_handle h, int k, int l, int ndir, const double* dh,
                                              const double* dB, double* F);
 
-/* Seconds spent in the last call and counters of the executor (GEMM calls,
- * tensor-core calls and their flops) since creation; any pointer may be NULL. */
+/* Counters of the handle's executor since creation: algorithmic flops and calls of the
+ * FP64 DFMA GEMMs (flops_fp64, gemms) and of the tensor-core contractions, split-bf16
+ * and FP64-grade alike (flops_tc, tc_gemms); any pointer may be NULL. */
 ccsd_status ccsd_stats(ccsd_handle h, double* flops_fp64, double* flops_tc, long long* gemms, long long* tc_gemms);
 
 /* One plain contraction C = alpha A B^T + beta C in one of the library's arithmetic forms,
