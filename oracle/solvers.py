@@ -441,6 +441,46 @@ class System:
             f += g0 * float(xe) + gam.dot(Vec(x1, x2))
         return f
 
+    # state energy gradients ------------------------------------------------
+    def energy_gradient(self, res: Result, k: int, h1, B1, tol_lin=1e-10):
+        """dE_k/dx along (h1, B1), orbitals fixed, from the energy Lagrangian.
+
+        The same construction as the coupling Lagrangian (Lagrangian section) with the
+        state energy in place of the overlap: E_0 + lambda.Omega for the ground state
+        (lambda^T A = -eta); for k >= 1, E_k = E_0 + omega_k and omega_k = L_k.(A R_k) is
+        stationary in L_k and R_k (biorthonormal eigenvectors, L_k.R_k = 1), so only its
+        amplitude dependence needs a multiplier: zeta^T A = -(F(L_k) R_k), and
+        domega_k/dx = L_k.(A^x R_k) + zeta.Omega^x at fixed t, L_k, R_k.
+        """
+        h1, B1 = cc.as_t(h1), cc.as_t(B1)
+        t = res.t
+        ox1, ox2, oe = cc.hamiltonian_derivative_residual(t.x1, t.x2, self.h, self.B, h1, B1, self.o, **self.kw)
+        om_x = Vec(ox1, ox2)
+        g = float(oe) + res.lam.dot(om_x)
+        if k > 0:
+            L, R = res.left[k - 1].vec, res.right[k - 1].vec
+            zeta, _ = self.solve_left_linear(t, self.hess_right(t, 0.0, L, R), tol=tol_lin)
+            x1, x2, _ = cc.hamiltonian_derivative_jacobian(t.x1, t.x2, R.x1, R.x2, self.h, self.B, h1, B1,
+                                                           self.o, **self.kw)
+            g += L.dot(Vec(x1, x2)) + zeta.dot(om_x)
+        return g
+
+    def energy_at(self, res0: Result, k: int, x: float, h1, B1, tol=1e-12):
+        """E_k(x): ground state from t(x0), root k matched by the largest |L_k(x0).R(x)|."""
+        sx = self.displaced(x, h1, B1)
+        tx, ex, _ = sx.solve_ground(tol=tol, t0=res0.t)
+        if k == 0:
+            return float(ex)
+        omega, R, _ = sx.eom_dense(tx, len(res0.omega) + 2)
+        Lk = res0.left[k - 1].vec
+        j = int(np.argmax([abs(Lk.dot(r)) for r in R]))
+        return float(ex) + float(omega[j])
+
+    def energy_gradient_fd(self, res0: Result, k: int, h1, B1, delta=2e-3):
+        """Central differences of E_k(x) with one Richardson step: error O(delta^4)."""
+        E = {s: self.energy_at(res0, k, s * delta, h1, B1) for s in (-2, -1, 1, 2)}
+        return (8.0 * (E[1] - E[-1]) - (E[2] - E[-2])) / (12.0 * delta)
+
     # finite differences of the definition ----------------------------------
     def displaced(self, x, h1, B1):
         return System(self.eps, self.h + x * cc.as_t(h1), self.B + x * cc.as_t(B1), self.o,
