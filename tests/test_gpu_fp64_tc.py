@@ -151,11 +151,3 @@ def test_fp64tc_pipeline_meets_fp64_tolerances():
         ref = S_.coupling(res, k, l, H.h1, H.B1, tol_lin=1e-12)
         assert abs(f - ref) < 1e-7 * abs(ref)
 
-
-def test_unknown_precision_is_rejected():
-    from paper_2301_13264_gb300.synth import make_hamiltonian
-
-    H = make_hamiltonian(2, 4, 6, seed=1)
-    with pytest.raises(B.CCSDError) as e:
-        B.ccsd_create(H.eps, H.h, H.B, H.o, H.v, H.naux, B.ccsd_default_options(precision=3))
-    assert e.value.status == B.ERR_ARG

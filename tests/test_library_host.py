@@ -60,6 +60,27 @@ def test_create_rejects_bad_arguments(L):
     with pytest.raises(binding.CCSDError) as e:
         binding.ccsd_create(H.eps, H.h, H.B, 2, 3, 4, opt)
     assert e.value.status == binding.ERR_ARG
+    opt = binding.ccsd_default_options(precision=3)  # FP64, MIXED or FP64_TC only
+    with pytest.raises(binding.CCSDError) as e:
+        binding.ccsd_create(H.eps, H.h, H.B, 2, 3, 4, opt)
+    assert e.value.status == binding.ERR_ARG
+    with pytest.raises(TypeError):
+        binding.ccsd_default_options(no_such_option=1)
+
+
+def test_fp64_tc_defaults_and_gemm_arguments(L):
+    opt = binding.ccsd_default_options()
+    assert opt.fp64_tc == 1
+    A, Bm = np.ones((3, 4)), np.ones((2, 4))
+    # checked before any device work: unknown form, beta outside {0, 1} on the tensor-core
+    # forms, split counts other than 2 and 3, mismatched K
+    for kw in (dict(form=7), dict(form=binding.GEMM_FP64_TC, beta=0.5), dict(form=binding.GEMM_SPLIT, splits=4)):
+        form = kw.pop("form")
+        with pytest.raises(binding.CCSDError) as e:
+            binding.ccsd_gemm(form, A, Bm, C=np.zeros((3, 2)), **kw)
+        assert e.value.status == binding.ERR_ARG
+    with pytest.raises(ValueError):
+        binding.ccsd_gemm(binding.GEMM_FP64, A, np.ones((2, 5)))
 
 
 @pytest.fixture(scope="module")
