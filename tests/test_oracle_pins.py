@@ -213,6 +213,27 @@ def test_adjointness_and_jacobian_is_derivative():
     assert (fd - ar).maxabs() < 1e-8
 
 
+def test_fmatrix_is_symmetric_and_the_derivative_of_the_jacobian():
+    """F(g) is the second derivative of g0 E + g.Omega: S.(F R) = R.(F S), and S.(F R) equals the
+    derivative of g0 eta.R + g.(A(t) R) along S (the F-matrix transformation of Eq. for F)."""
+    o, v = 2, 4
+    H = make_hamiltonian(o, v, 8, seed=14)
+    S = System(H.eps, H.h, H.B, o)
+    X1, X2 = random_amplitudes(o, v, 15, scale=0.05, nvec=4)
+    t, g, r, s_ = (Vec(T(X1[k]), T(X2[k])) for k in range(4))
+    for g0 in (0.0, 0.6):
+        fr = S.hess_right(t, g0, g, r)
+        fs = S.hess_right(t, g0, g, s_)
+        assert abs(s_.dot(fr) - r.dot(fs)) < 1e-14 * max(1.0, abs(s_.dot(fr)))
+        d = 1e-4
+
+        def lin(x):
+            return g0 * S.eta(x).dot(r) + g.dot(S.right(x, r))
+
+        fd = (lin(t + s_ * d) - lin(t - s_ * d)) / (2 * d)
+        assert abs(fd - s_.dot(fr)) < 1e-8 * max(1.0, abs(fd))
+
+
 def test_davidson_matches_dense(small_system):
     H, S, res = small_system
     omega, R, L = S.eom(res.t, 3, dense=False, tol=1e-10)
