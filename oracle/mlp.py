@@ -20,7 +20,7 @@ mean[3], scale[3], tscale.  The first 17153 entries are trainable.
 
 Nothing here is in the paper: the starting point of the amplitude iterations does
 not change the solution the CCSD equations define, so the converged residual is
-the criterion the learned start is judged by.
+the criterion the learned start is evaluated by.
 """
 from __future__ import annotations
 
