@@ -18,7 +18,14 @@ ccsd      : closed-shell CCSD residual and energy over Cholesky-factored
 solvers   : ground-state amplitudes, ground-state multipliers, EOM left/right
             states, biorthonormalisation, the coupling multipliers and the
             derivative coupling of Eq. (NAC_NC), plus a finite-difference
-            evaluation of the definition Eq. (nac).
+            evaluation of the definition Eq. (nac); state-energy gradients
+            from the energy Lagrangian and finite differences of E_k(x).
+relaxed   : Hartree-Fock orbitals, the orbital-response multipliers and the
+            relaxed coupling.
+meci      : the crossing-point search the couplings serve (branching plane
+            from the energy-difference gradient and the coupling,
+            Bearpark-Robb-Schlegel direction) on a synthetic family, from the
+            CC oracle or from full CI.
 mlp       : the learned doubles guess (features, network, gradients of its
             training loss), an extension outside the paper's method.
 """
