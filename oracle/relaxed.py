@@ -181,6 +181,56 @@ def relaxed_coupling(S: System, res, i: int, j: int, h1, B1, tol_lin=1e-10):
     return f0 + float(kbar @ fx.reshape(-1)), kbar.reshape(ke.shape)
 
 
+def _rotation_integrals(S: System, ii: int, a: int):
+    """(dh, dB) of the integrals along the rotation kappa_ia at kappa = 0."""
+    K = rotation_direction(S.o, S.n, ii, a)
+    dh = K.T @ S.h + S.h @ K
+    dB = torch.einsum("rp,Jrq->Jpq", K, S.B) + torch.einsum("Jpr,rq->Jpq", S.B, K)
+    return dh, dB
+
+
+def relaxed_energy_gradient(S: System, res, k: int, h1, B1, tol_lin=1e-10):
+    """dE_k/dx with the Hartree-Fock orbitals following x: the energy Lagrangian gains
+    kappa-bar.F_ov with kappa-bar^T A^HF = -(k-eta_E)^T, k-eta_E the derivative of the energy
+    Lagrangian along each occupied-virtual rotation of the integrals (no overlap term)."""
+    o, v = S.o, S.n - S.o
+    zeta = S.energy_multiplier(res, k, tol_lin)
+    g0 = S.energy_lagrangian_derivative(res, k, zeta, h1, B1)
+    ke = torch.zeros((o, v), dtype=F64)
+    for ii in range(o):
+        for a in range(v):
+            ke[ii, a] = S.energy_lagrangian_derivative(res, k, zeta, *_rotation_integrals(S, ii, a))
+    A = hf_hessian(S.h, S.B, o)
+    kbar = -torch.linalg.solve(A.T, ke.reshape(-1))
+    h1, B1 = cc.as_t(h1), cc.as_t(B1)
+    _, fx = torch.func.jvp(lambda hh, BB: fock(hh, BB, o)[:o, o:], (S.h, S.B), (h1, B1))
+    return g0 + float(kbar @ fx.reshape(-1))
+
+
+def relaxed_energy_fd(h0, B0, h1, B1, o: int, k: int, nroots: int, delta=2e-3):
+    """dE_k/dx by central differences (one Richardson step) with the Hartree-Fock orbitals
+    re-optimised at every displacement; the root is followed by |L_k(x0).R(x)| (amplitudes in
+    the rotated orbitals, a small rotation).  (h0, B0) must be Hartree-Fock at x0."""
+    h0, B0, h1, B1 = (np.asarray(a, dtype=np.float64) for a in (h0, B0, h1, B1))
+    eps = np.diag(np.asarray(fock(h0, B0, o)))
+    S0 = System(eps, h0, B0, o)
+    res0 = S0.run(nroots, dense=True, tol=1e-13, tol_lin=1e-13)
+
+    def energy(x):
+        _, _, hr, Br = scf(h0 + x * h1, B0 + x * B1, o)
+        Sx = System(eps, hr, Br, o)
+        tx, ex, _ = Sx.solve_ground(tol=1e-13, t0=res0.t)
+        if k == 0:
+            return float(ex)
+        omega, R, _ = Sx.eom_dense(tx, nroots + 2)
+        Lk = res0.left[k - 1].vec
+        j = int(np.argmax([abs(Lk.dot(r)) for r in R]))
+        return float(ex) + float(omega[j])
+
+    E = {s: energy(s * delta) for s in (-2, -1, 1, 2)}
+    return (8.0 * (E[1] - E[-1]) - (E[2] - E[-2])) / (12.0 * delta), S0, res0
+
+
 # ---------------------------------------------------------------------------
 # finite differences of the definition in determinant space (tiny systems)
 # ---------------------------------------------------------------------------

@@ -452,17 +452,29 @@ class System:
         amplitude dependence needs a multiplier: zeta^T A = -(F(L_k) R_k), and
         domega_k/dx = L_k.(A^x R_k) + zeta.Omega^x at fixed t, L_k, R_k.
         """
-        h1, B1 = cc.as_t(h1), cc.as_t(B1)
+        return self.energy_lagrangian_derivative(res, k, self.energy_multiplier(res, k, tol_lin), h1, B1)
+
+    def energy_multiplier(self, res: Result, k: int, tol_lin=1e-10):
+        """zeta of the excited-state energy Lagrangian, zeta^T A = -(F(L_k) R_k); None for k = 0."""
+        if k == 0:
+            return None
+        L, R = res.left[k - 1].vec, res.right[k - 1].vec
+        zeta, _ = self.solve_left_linear(res.t, self.hess_right(res.t, 0.0, L, R), tol=tol_lin)
+        return zeta
+
+    def energy_lagrangian_derivative(self, res: Result, k: int, zeta, dh, dB) -> float:
+        """Derivative of the energy Lagrangian of state k along (dh, dB) at fixed amplitudes and
+        multipliers: E^x + lambda.Omega^x, plus L_k.(A^x R_k) + zeta.Omega^x for k >= 1."""
+        dh, dB = cc.as_t(dh), cc.as_t(dB)
         t = res.t
-        ox1, ox2, oe = cc.hamiltonian_derivative_residual(t.x1, t.x2, self.h, self.B, h1, B1, self.o, **self.kw)
+        ox1, ox2, oe = cc.hamiltonian_derivative_residual(t.x1, t.x2, self.h, self.B, dh, dB, self.o, **self.kw)
         om_x = Vec(ox1, ox2)
-        g = float(oe) + res.lam.dot(om_x)
+        g = float(oe) + float(res.lam.dot(om_x))
         if k > 0:
             L, R = res.left[k - 1].vec, res.right[k - 1].vec
-            zeta, _ = self.solve_left_linear(t, self.hess_right(t, 0.0, L, R), tol=tol_lin)
-            x1, x2, _ = cc.hamiltonian_derivative_jacobian(t.x1, t.x2, R.x1, R.x2, self.h, self.B, h1, B1,
+            x1, x2, _ = cc.hamiltonian_derivative_jacobian(t.x1, t.x2, R.x1, R.x2, self.h, self.B, dh, dB,
                                                            self.o, **self.kw)
-            g += L.dot(Vec(x1, x2)) + zeta.dot(om_x)
+            g += float(L.dot(Vec(x1, x2))) + float(zeta.dot(om_x))
         return g
 
     def energy_at(self, res0: Result, k: int, x: float, h1, B1, tol=1e-12):

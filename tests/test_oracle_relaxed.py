@@ -7,7 +7,9 @@ theorem holds in determinant space.  The transition density equals
 equals finite differences of the definition with the orbitals re-optimised at every
 displacement and the ket mapped back by the many-body rotation operator, and for
 two electrons (CCSD = full CI, which does not depend on the orbitals) it equals the
-unrelaxed coupling.
+unrelaxed coupling.  The same holds for the state-energy gradients with the orbital
+term: finite differences of E_k(x) with re-optimised orbitals, and relaxed = unrelaxed
+for two electrons.
 """
 import numpy as np
 import pytest
@@ -107,3 +109,25 @@ def test_two_electrons_relaxed_equals_unrelaxed():
         f, _ = rx.relaxed_coupling(S, res, i, j, h1, B1, tol_lin=1e-13)
         f0 = S.coupling(res, i, j, h1, B1, tol_lin=1e-13)
         assert abs(f - f0) < 1e-9 * max(1.0, abs(f0))
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_relaxed_energy_gradient_equals_finite_differences(k):
+    """dE_k/dx with the orbitals re-optimised at every displacement (energies only, no states
+    mapped between orbital sets) against the Lagrangian with the kappa-bar term."""
+    o, v, naux = 2, 3, 8
+    h0, B0, h1, B1 = _hf_system(o, v, naux, seed=6, bscale=0.4)
+    fd, S, res = rx.relaxed_energy_fd(h0, B0, h1, B1, o, k, nroots=2)
+    g = rx.relaxed_energy_gradient(S, res, k, h1, B1, tol_lin=1e-13)
+    assert abs(g - fd) < 1e-9
+    assert abs(g - S.energy_gradient(res, k, h1, B1, tol_lin=1e-13)) > 1e-7
+
+
+def test_two_electrons_relaxed_energy_gradient_equals_unrelaxed():
+    o, v, naux = 1, 4, 7
+    h0, B0, h1, B1 = _hf_system(o, v, naux, seed=7)
+    S = System(np.diag(rx.fock(h0, B0, o).numpy()), h0, B0, o)
+    res = S.run(3, dense=True, tol=1e-13, tol_lin=1e-13)
+    for k in range(4):
+        g = rx.relaxed_energy_gradient(S, res, k, h1, B1, tol_lin=1e-13)
+        assert abs(g - S.energy_gradient(res, k, h1, B1, tol_lin=1e-13)) < 1e-9 * max(1.0, abs(g))
