@@ -391,8 +391,8 @@ int solve_left_linear(ccsd_ctx* c, const double* rhs, double* x, double tol, boo
 class Davidson {
  public:
   Davidson(ccsd_ctx* c, int side, int nroots, double tol, const std::vector<std::unique_ptr<DevBuf>>* init)
-      : c_(c),
-        side(side),
+      : side(side),
+        c_(c),
         nroots_(nroots),
         tol_(tol),
         dim_(c->dim),
