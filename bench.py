@@ -185,15 +185,62 @@ def oracle_sample(steps=1):
     return times, H, torch.get_num_threads()
 
 
+def cpu_model():
+    """The host CPU's model name (/proc/cpuinfo, else lscpu, else the machine type)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        import subprocess
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_one_thread_sample():
+    """Seconds for one oracle right transform on one thread, at a smaller shape (o=33, v=60,
+    naux=300) that keeps the single-thread run to seconds."""
+    import torch
+    from oracle.solvers import System, Vec
+    from paper_2301_13264_gb300.synth import make_hamiltonian, random_amplitudes
+    H = make_hamiltonian(33, 60, 300, seed=0)
+    S = System(H.eps, H.h, H.B, H.o)
+    X1, X2 = random_amplitudes(H.o, H.v, 31, scale=0.01, nvec=2)
+    t = Vec(torch.as_tensor(X1[0]), torch.as_tensor(X2[0]))
+    r = Vec(torch.as_tensor(X1[1]), torch.as_tensor(X2[1]))
+    n0 = torch.get_num_threads()
+    torch.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        S.right(t, r)
+        return time.perf_counter() - t0, H
+    finally:
+        torch.set_num_threads(n0)
+
+
 def cpu_baseline_entry(o, v, naux):
     times, Hs, threads = oracle_sample(1)
     f_small, _ = transform_flops(Hs.o, Hs.v, Hs.naux)
     f_full, _ = transform_flops(o, v, naux)
     rate = (1.0 / times[-1]) * f_small / f_full
-    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+    t1, H1 = oracle_one_thread_sample()
+    f_one, _ = transform_flops(H1.o, H1.v, H1.naux)
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
             "sample": (f"one oracle (numpy/torch FP64) right transform at o={Hs.o},v={Hs.v},naux={Hs.naux} took "
                        f"{times[-1]:.1f} s; scaled to o={o},v={v},naux={naux} by the ratio of algorithmic flops "
-                       f"({f_small:.3g} / {f_full:.3g})")}
+                       f"({f_small:.3g} / {f_full:.3g})"),
+            "one_thread": {"value": (1.0 / t1) * f_one / f_full, "unit": UNIT, "cores": 1,
+                           "sample": (f"one right transform at o={H1.o},v={H1.v},naux={H1.naux} on one thread took "
+                                      f"{t1:.1f} s; scaled by the algorithmic flop ratio")}}
 
 
 def run_reference(args, rank, world):
@@ -220,7 +267,8 @@ def run_reference(args, rank, world):
            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": f"{args.workload} o={o} v={v} naux={naux}", "side": "right"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                            "cpu_model": cpu_model()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
