@@ -1,0 +1,73 @@
+"""The benchmark's control flow and JSON line on the CPU, with the device and the library faked.
+
+Every call the benchmark makes into CUDA or the library is replaced by a stand-in that records
+its arguments (no device work happens); the test checks that the default transform benchmark
+times blocks of nvec and of 1 vector on both sides and prints one JSON line with the keys the
+measurement contract needs.
+"""
+import json
+import os
+import runpy
+import sys
+
+import torch
+
+from paper_2301_13264_gb300 import binding as B
+import paper_2301_13264_gb300.synth as synth
+
+
+class _Event:
+    def __init__(self, **kw):
+        self.t = 0.0
+
+    def record(self, *a):
+        import time
+        self.t = time.perf_counter()
+
+    def elapsed_time(self, other):
+        return max((other.t - self.t) * 1e3, 1e-3)
+
+
+class _Stream:
+    cuda_stream = 0
+
+
+def test_transform_benchmark_json(monkeypatch, capsys):
+    calls = []
+
+    def transform(h, side, nv, X, Y):
+        assert X.is_contiguous() and Y.is_contiguous() and X.shape[0] >= nv and Y.shape[0] >= nv
+        calls.append((side, nv))
+
+    as_tensor = torch.as_tensor
+    monkeypatch.setattr(torch, "as_tensor", lambda x, *a, **k: as_tensor(x, *a, **{q: w for q, w in k.items()
+                                                                                   if q != "device"}))
+    monkeypatch.setattr(torch.cuda, "Event", _Event)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "set_device", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: _Stream())
+    monkeypatch.setattr(B, "ccsd_create", lambda *a, **k: object())
+    monkeypatch.setattr(B, "ccsd_solve_ground", lambda h: (-1.0, 3))
+    monkeypatch.setattr(B, "ccsd_jacobian_transform", transform)
+    monkeypatch.setattr(B, "ccsd_profile_start", lambda h: None)
+    monkeypatch.setattr(B, "ccsd_profile_stop", lambda h: {k: 1.0 for k, _ in B.ProfileData._fields_})
+    monkeypatch.setattr(B, "ccsd_destroy", lambda h: None)
+    monkeypatch.setattr(synth, "workload", lambda name: synth.make_hamiltonian(2, 4, 6, seed=0))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--no-e2e", "--no-cpu-baseline", "--steps", "2", "--warmup", "3",
+                                      "--nvec", "3"])
+    runpy.run_path(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"),
+                   run_name="__main__")
+    line = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(line) == 1
+    out = json.loads(line[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "roofline", "gpu_launches", "clocks",
+                "right_transforms_per_s", "left_transforms_per_s", "block1_transforms_per_s"):
+        assert key in out, key
+    assert out["steps"] == 2 and out["warmup"] == 3 and out["n_gpus"] == 1
+    for key in ("bound", "achieved", "peak", "unit", "frac", "traffic", "frac_of_fp64_peak"):
+        assert key in out["roofline"], key
+    # warm-up and timed steps (3 + 2 steps of right + left at nvec), the two separate 8-vector runs per
+    # side, then one untimed and two timed single-vector transforms per side
+    assert calls[:10] == [(0, 3), (1, 3)] * 5
+    assert calls.count((0, 1)) == 3 and calls.count((1, 1)) == 3
