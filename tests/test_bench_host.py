@@ -71,3 +71,30 @@ def test_transform_benchmark_json(monkeypatch, capsys):
     # side, then one untimed and two timed single-vector transforms per side
     assert calls[:10] == [(0, 3), (1, 3)] * 5
     assert calls.count((0, 1)) == 3 and calls.count((1, 1)) == 3
+
+
+def test_time_to_coupling_json(monkeypatch, capsys):
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    created = []
+
+    def create(eps, h, Bm, o, v, naux, opt):
+        created.append(opt.precision)
+        return object()
+
+    monkeypatch.setattr(B, "ccsd_create", create)
+    monkeypatch.setattr(B, "ccsd_solve_ground", lambda h: (-1.0, 3))
+    monkeypatch.setattr(B, "eom_solve_right", lambda h, n: ([0.3, 0.4], 5))
+    monkeypatch.setattr(B, "eom_solve_left", lambda h, n: ([0.3, 0.4], 6))
+    monkeypatch.setattr(B, "ccsd_derivative_coupling", lambda h, k, l, nd, dh, dB: [0.01 * (k + 2 * l)])
+    monkeypatch.setattr(B, "ccsd_stats", lambda h: {"flops_fp64": 1.0, "flops_tc": 2.0, "gemms": 3, "tc_gemms": 4})
+    monkeypatch.setattr(B, "ccsd_destroy", lambda h: None)
+    monkeypatch.setattr(synth, "workload", lambda name: synth.make_hamiltonian(2, 4, 6, seed=0))
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--ttc", "mixed,fp64tc,fp64", "--workload", "thymine_dz"])
+    runpy.run_path(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"),
+                   run_name="__main__")
+    out = json.loads([l for l in capsys.readouterr().out.splitlines() if l.startswith("{")][0])
+    assert created == [B.PREC_MIXED, B.PREC_FP64_TC, B.PREC_FP64]
+    assert set(out["forms"]) == {"mixed", "fp64tc", "fp64"}
+    for form in ("mixed", "fp64tc"):
+        cmp = out["forms"][form]["vs_fp64"]
+        assert cmp["energy_diff"] == 0.0 and cmp["coupling_rel_diff"] == 0.0 and cmp["speedup"] > 0
