@@ -272,8 +272,17 @@ class System:
         L = [Vec(*unpack(torch.as_tensor(Vl[:, k].real), self.o, self.v)) for k in orderl]
         return omega, R, L
 
-    def davidson(self, apply, nroots, tol=1e-9, maxit=200, maxsub=None, guesses=None):
-        """Block Davidson for the lowest nroots (by real part) of a non-symmetric map."""
+    def davidson(self, apply, nroots, tol=1e-9, maxit=200, maxsub=None, guesses=None, max_complex=12):
+        """Block Davidson for the lowest nroots (by real part) of a non-symmetric map.
+
+        A small subspace of a non-symmetric map can give a complex-conjugate pair of
+        Ritz values among the wanted ones even when the converged roots are real.
+        Such a pair is treated as transient: the subspace is expanded with the
+        preconditioned real and imaginary parts of the pair's residual (the real
+        2-D invariant subspace of the pair), and the solve fails only when a
+        complex pair stays among the wanted roots for more than `max_complex`
+        consecutive expansions.  A complex wanted root never counts as converged.
+        """
         o, v = self.o, self.v
         maxsub = maxsub or max(8 * nroots, 24)
         if guesses is None:
@@ -298,31 +307,44 @@ class System:
             AV.append(apply(x))
             return True
 
+        def combine(basis, u):
+            x = basis[0] * u[0]
+            for a in range(1, len(basis)):
+                x = x + basis[a] * u[a]
+            return x
+
         for g in guesses:
             add(g)
+        n_complex = 0
         for it in range(1, maxit + 1):
             m = len(V)
             G = np.array([[V[a].dot(AV[b]) for b in range(m)] for a in range(m)])
             w, U = np.linalg.eig(G)
             order = np.argsort(w.real)[:nroots]
-            if np.abs(w[order].imag).max() > 1e-8:
+            is_complex = np.abs(w[order].imag) > 1e-8
+            n_complex = n_complex + 1 if is_complex.any() else 0
+            if n_complex > max_complex:
                 raise RuntimeError("complex root among the wanted roots")
-            X, res, ok = [], [], True
+            X, res, ok = [], [], not is_complex.any()
             for k in order:
-                u = U[:, k].real
-                x = V[0] * u[0]
-                ax = AV[0] * u[0]
-                for a in range(1, m):
-                    x = x + V[a] * u[a]
-                    ax = ax + AV[a] * u[a]
-                r = ax - x * w[k].real
-                X.append(x)
-                res.append((r, w[k].real))
-                if r.norm() > tol:
-                    ok = False
+                wr, wi = w[k].real, w[k].imag
+                ur, ui = U[:, k].real, U[:, k].imag
+                xr, axr = combine(V, ur), combine(AV, ur)
+                if abs(wi) <= 1e-8:
+                    r = axr - xr * wr
+                    X.append(xr)
+                    res.append((r, wr))
+                    if r.norm() > tol:
+                        ok = False
+                    continue
+                # complex Ritz pair: A(xr + i xi) - (wr + i wi)(xr + i xi), real and imaginary parts
+                xi, axi = combine(V, ui), combine(AV, ui)
+                X.extend([xr, xi])
+                res.append((axr - xr * wr + xi * wi, wr))
+                res.append((axi - xi * wr - xr * wi, wr))
             if ok:
                 return np.array([w[k].real for k in order]), X, it
-            if m + nroots > maxsub:
+            if m + len(res) > maxsub:
                 V.clear()
                 AV.clear()
                 for x in X:

@@ -269,3 +269,21 @@ def test_orbital_rotation_invariance():
         p1 = (S1.coupling(r1, i, j, rot(H.h1), rotB(H.B1), tol_lin=1e-12)
               * S1.coupling(r1, j, i, rot(H.h1), rotB(H.B1), tol_lin=1e-12))
         assert abs(p0 - p1) < 1e-8 * abs(p0)
+
+
+def test_davidson_survives_transient_complex_pair():
+    """A small Davidson subspace of the non-symmetric left Jacobian gives a complex Ritz pair
+    among the wanted roots of this system (o=3, v=6, naux=9, seed 5), although the two lowest
+    roots are real.  With no complex expansion allowed the solve fails, which shows the pair
+    occurs; with the default rule it converges to the dense diagonalisation's roots and vectors."""
+    H = make_hamiltonian(3, 6, 9, seed=5)
+    S = System(H.eps, H.h, H.B, 3)
+    t, _, _ = S.solve_ground(tol=1e-12)
+    with pytest.raises(RuntimeError, match="complex root"):
+        S.davidson(lambda x: S.left(t, x), 2, tol=1e-10, max_complex=0)
+    omega_d, R_d, L_d = S.eom(t, 2, dense=True)
+    omega, R, L = S.eom(t, 2, dense=False, tol=1e-10)
+    assert np.abs(np.array(omega) - np.array(omega_d)).max() < 1e-10
+    for k in range(2):
+        assert (R[k].vec - R_d[k].vec).maxabs() < 1e-8
+        assert (L[k].vec - L_d[k].vec).maxabs() < 1e-8
