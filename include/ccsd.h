@@ -250,15 +250,18 @@ void ccsd_batch_destroy(ccsd_batch b);
  * F[d] = sum_pq D_pq dh[d]_pq + sum_Jpq Z_Jpq dB[d]_Jpq with the densities the
  * handle already holds: call ccsd_coupling_densities(h, k, l, ...) first,
  * otherwise CCSD_ERR_STATE.  dh[ndir][n*n] and dB[ndir][naux*n*n] must be device
- * memory (CCSD_ERR_ARG otherwise); F[ndir] may be host or device memory.
+ * memory of the handle's GPU (the one current at ccsd_create; CCSD_ERR_ARG
+ * otherwise); F[ndir] may be host or device memory.
  * 1 <= ndir <= 256 (CCSD_ERR_ARG otherwise).
  * Allocates nothing: the reduction scratch is a fixed 16 KiB array in the
  * library's device image (one per GPU that loads the library, kept until the
- * process exits).  Its device address is looked up on the first call made on
- * each device, with that device current: make that first call before any CUDA
- * stream capture.  All calls share the array, so calls whose GPU work overlaps
- * (different streams or threads) race and may return wrong values; serialise
- * them.  Synchronises the handle's stream. */
+ * process exits).  Its device address is looked up on the first call made for
+ * each device, with the handle's device made current for the call (the
+ * caller's current device is restored on return): make that first call before
+ * any CUDA stream capture.  All calls share the array, so calls whose GPU work
+ * overlaps (different streams or threads) race and may return wrong values;
+ * serialise them.  Launches 4 * ndir + 1 kernels on the handle's stream and
+ * synchronises that stream before returning. */
 ccsd_status ccsd_derivative_coupling_noalloc(ccsd_handle h, int k, int l, int ndir, const double* dh,
                                              const double* dB, double* F);
 

@@ -371,11 +371,16 @@ class System:
     def eom(self, t: Vec, nroots: int, dense=False, tol=1e-9):
         if dense:
             omega, R, L = self.eom_dense(t, nroots)
-        else:
-            omega, R, _ = self.davidson(lambda x: self.right(t, x), nroots, tol=tol)
-            omega_l, L, _ = self.davidson(lambda x: self.left(t, x), nroots, tol=tol)
-            if np.abs(omega - omega_l).max() > 1e-6:
-                raise RuntimeError("left and right EOM roots differ")
+            return self.eom_from_vectors(t, omega, R, omega, L)
+        omega, R, _ = self.davidson(lambda x: self.right(t, x), nroots, tol=tol)
+        omega_l, L, _ = self.davidson(lambda x: self.left(t, x), nroots, tol=tol)
+        return self.eom_from_vectors(t, omega, R, omega_l, L)
+
+    def eom_from_vectors(self, t: Vec, omega, R, omega_l, L):
+        """Biorthonormal states from right and left eigenvectors of the same roots."""
+        nroots = len(R)
+        if np.abs(np.asarray(omega) - np.asarray(omega_l)).max() > 1e-6:
+            raise RuntimeError("left and right EOM roots differ")
         R = [self.normalize_right(r) for r in R]
         # biorthonormalise: L_k^T R_l = delta_kl (roots are non-degenerate).
         # With M[m, l] = <L_m|R_l> and L'_k = sum_m c[m, k] L_m, <L'_k|R_l> = (c^T M)[k, l],

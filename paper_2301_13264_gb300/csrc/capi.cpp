@@ -84,6 +84,7 @@ struct ccsd_ctx {
   VecShape vs;
   int64_t dim = 0, n1 = 0;
   cudaStream_t st = 0;
+  int device = 0;  // the GPU that was current at ccsd_create: all of the handle's memory lives there
   Programs P;
   std::unique_ptr<Executor> ex;
   DevBuf eps, h, B, ones;
@@ -1317,6 +1318,7 @@ ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int
     c->n1 = (int64_t)o * v;
     c->dim = c->vs.dim();
     c->st = (cudaStream_t)c->opt.stream;
+    CUDA_OK(cudaGetDevice(&c->device));
     // symmetry of the inputs
     {
       const int64_t n = c->n;
@@ -1661,15 +1663,16 @@ ccsd_status ccsd_stats(ccsd_handle c, double* flops_fp64, double* flops_tc, long
 
 namespace ccsd {
 // Internal accessor for noalloc.cu: the densities of the pair (k, l) if they are
-// the ones held by the handle, with the sizes and stream.  Allocates nothing.
+// the ones held by the handle, with the sizes, stream and device.  Allocates nothing.
 bool held_densities(ccsd_handle c, int k, int l, const double** D, const double** Z, int* n, int* naux,
-                    cudaStream_t* st) {
+                    cudaStream_t* st, int* device) {
   if (!c || c->dens_k != k || c->dens_l != l || !c->Dd.p || !c->Zd.p) return false;
   *D = c->Dd.p;
   *Z = c->Zd.p;
   *n = c->n;
   *naux = c->naux;
   *st = c->st;
+  *device = c->device;
   return true;
 }
 void set_error(ccsd_handle c, const char* msg) {

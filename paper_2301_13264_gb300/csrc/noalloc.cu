@@ -13,7 +13,8 @@
 // Every GPU that loads the library holds it until the process exits.  Host
 // code cannot use the array's name as a device address, so the address is
 // looked up once per device with cudaGetSymbolAddress, with that device
-// current, and cached here.
+// current, and cached here.  The device is the handle's (the one current when
+// the handle was created), not whichever device is current at the call.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -23,7 +24,7 @@
 
 namespace ccsd {
 bool held_densities(ccsd_handle c, int k, int l, const double** D, const double** Z, int* n, int* naux,
-                    cudaStream_t* st);
+                    cudaStream_t* st, int* device);
 void set_error(ccsd_handle c, const char* msg);
 }  // namespace ccsd
 
@@ -40,11 +41,10 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 double* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once).
-double* scratch_for_current_device(cudaError_t* err) {
-  int dev = -1;
-  *err = cudaGetDevice(&dev);
-  if (*err != cudaSuccess) return nullptr;
+// Device address of the scratch array on GPU `dev`, which must be current (looked up
+// once per device and cached).
+double* scratch_for_device(int dev, cudaError_t* err) {
+  *err = cudaSuccess;
   if (dev < 0 || dev >= kMaxDevices) {
     *err = cudaErrorInvalidDevice;
     return nullptr;
@@ -64,14 +64,33 @@ __global__ void k_add_parts(int ndir, const double* h_part, const double* b_part
   if (d < ndir) out[d] = h_part[d] + b_part[d];
 }
 
-bool on_device(const void* p) {
+// true when p is device (or managed) memory of GPU `dev`: the kernels below read it
+// from the handle's device and no peer access is set up
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
+
+// Makes GPU `dev` current for the guard's lifetime (the handle's stream belongs to it)
+// and restores the caller's device afterwards.  Allocates nothing.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+    if (err != cudaSuccess) prev = -1;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
 
 }  // namespace
 
@@ -86,16 +105,22 @@ extern "C" ccsd_status ccsd_derivative_coupling_noalloc(ccsd_handle h, int k, in
   const double *D = nullptr, *Z = nullptr;
   int n = 0, naux = 0;
   cudaStream_t st = 0;
-  if (!held_densities(h, k, l, &D, &Z, &n, &naux, &st)) {
+  int dev = 0;
+  if (!held_densities(h, k, l, &D, &Z, &n, &naux, &st, &dev)) {
     set_error(h, "noalloc coupling: call ccsd_coupling_densities for this (k, l) first");
     return CCSD_ERR_STATE;
   }
-  if (!on_device(dh) || !on_device(dB)) {
-    set_error(h, "noalloc coupling: dh and dB must be device memory");
+  DeviceGuard on_handle_device(dev);
+  if (on_handle_device.err != cudaSuccess) {
+    set_error(h, cudaGetErrorString(on_handle_device.err));
+    return CCSD_ERR_CUDA;
+  }
+  if (!on_device(dh, dev) || !on_device(dB, dev)) {
+    set_error(h, "noalloc coupling: dh and dB must be device memory of the handle's GPU");
     return CCSD_ERR_ARG;
   }
   cudaError_t err = cudaSuccess;
-  double* s = scratch_for_current_device(&err);
+  double* s = scratch_for_device(dev, &err);
   if (!s) {
     set_error(h, cudaGetErrorString(err));
     return CCSD_ERR_CUDA;
@@ -105,7 +130,8 @@ extern "C" ccsd_status ccsd_derivative_coupling_noalloc(ccsd_handle h, int k, in
   double* b_part = h_part + kMaxDirections;
   double* sum = b_part + kMaxDirections;
   const long long nn = (long long)n * n, nb = (long long)naux * nn;
-  // every slot used below is written before it is read, so nothing is cleared
+  // every slot used below is written before it is read, so nothing is cleared;
+  // launch_dot counts its own two launches, so the call launches 4 * ndir + 1 kernels
   for (int d = 0; d < ndir; ++d) {
     launch_dot(nn, D, dh + d * nn, h_part + d, partials, st);
     launch_dot(nb, Z, dB + d * nb, b_part + d, partials, st);

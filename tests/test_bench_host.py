@@ -8,6 +8,7 @@ measurement contract needs.
 import json
 import os
 import runpy
+import subprocess
 import sys
 
 import torch
@@ -98,3 +99,38 @@ def test_time_to_coupling_json(monkeypatch, capsys):
     for form in ("mixed", "fp64tc"):
         cmp = out["forms"][form]["vs_fp64"]
         assert cmp["energy_diff"] == 0.0 and cmp["coupling_rel_diff"] == 0.0 and cmp["speedup"] > 0
+
+
+def test_transform_flops_count_the_ladder_packed():
+    """The ladder enters at its pair-packed size, o^2 v^4 / 4 multiply-adds per vector;
+    at o=33, v=228, naux=900 one transform is about 10.2 TFLOP of algorithmic work."""
+    bench = runpy.run_path(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"))
+    for (o, v, naux) in [(2, 5, 7), (33, 228, 900)]:
+        total, ladder = bench["transform_flops"](o, v, naux)
+        assert ladder == 2.0 * o * o * v ** 4 / 4.0
+        assert total > ladder
+    total, _ = bench["transform_flops"](33, 228, 900)
+    assert 9.5e12 < total < 11e12
+
+
+def test_reference_arm_loads_nothing_of_the_library(tmp_path):
+    """The reference arm runs the oracle alone: neither the binding module nor the CUDA
+    library may be loaded in its process."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    probe = tmp_path / "probe.py"
+    probe.write_text(
+        "import json, runpy, sys\n"
+        f"sys.path.insert(0, {root!r})\n"
+        "sys.argv = ['bench.py', '--impl', 'reference', '--workload', 'small', '--steps', '5', '--warmup', '1']\n"
+        f"runpy.run_path({os.path.join(root, 'bench.py')!r}, run_name='__main__')\n"
+        "maps = open('/proc/self/maps').read()\n"
+        "assert 'libccsd_gb300' not in maps, 'CUDA library loaded'\n"
+        "assert 'paper_2301_13264_gb300.binding' not in sys.modules, 'binding imported'\n"
+        "print('CLEAN')\n")
+    r = subprocess.run([sys.executable, str(probe)], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    line = [l for l in r.stdout.splitlines() if l.startswith("{")][0]
+    out = json.loads(line)
+    assert out["impl"] == "reference" and out["steps"] == 2 and out["steps_requested"] == 5
+    assert out["value"] > 0 and out["cpu_baseline"]["kind"] == "oracle"
+    assert "CLEAN" in r.stdout

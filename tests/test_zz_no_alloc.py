@@ -38,7 +38,14 @@ def test_noalloc_coupling_matches_regular_entry_point_twice():
             ref = B.ccsd_derivative_coupling(h, k, l, 3, dh_d, dB_d)
             B.ccsd_coupling_densities(h, k, l, np.zeros((n, n)))
             first = B.ccsd_derivative_coupling_noalloc(h, k, l, 3, dh_d, dB_d)
+            torch.cuda.synchronize()
+            free_before = torch.cuda.mem_get_info()[0]
+            B.ccsd_profile_start(h)
             second = B.ccsd_derivative_coupling_noalloc(h, k, l, 3, dh_d, dB_d)
+            launched = B.ccsd_profile_stop(h)["launches"]
+            # the second call changes nothing in the device's free memory
+            assert torch.cuda.mem_get_info()[0] == free_before
+            assert launched == 4 * 3 + 1
             for got in (first, second):
                 for a, b in zip(got, ref):
                     assert abs(a - b) <= 1e-12 * max(1.0, abs(b))
@@ -48,6 +55,9 @@ def test_noalloc_coupling_matches_regular_entry_point_twice():
         assert e.value.status == B.ERR_STATE
         with pytest.raises(B.CCSDError) as e:
             B.ccsd_derivative_coupling_noalloc(h, 0, 1, 1, dh, dB)
+        assert e.value.status == B.ERR_ARG
+        with pytest.raises(B.CCSDError) as e:
+            B.ccsd_derivative_coupling_noalloc(h, 0, 1, 257, dh_d, dB_d)
         assert e.value.status == B.ERR_ARG
     finally:
         B.ccsd_destroy(h)
