@@ -93,6 +93,19 @@ typedef struct {
                            tc_min_flops as FP64-grade tensor-core products (1, default: 7 fixed-point
                            bf16 slices per operand, exact FP32 sums per K chunk, integer accumulation;
                            error about 2^-46 max|A_m.| max|B_n.| per K term) or as FP64 DFMA (0) */
+  /* Device memory: when alloc and free are both set, every device allocation the handle
+   * makes (at creation, in its calls and for its caches) goes through them; both NULL (the
+   * default): the CUDA runtime (cudaMalloc / cudaMallocAsync); one of them NULL: CCSD_ERR_ARG.
+   * alloc(bytes, stream, alloc_ctx) returns memory of the handle's GPU that work queued on
+   * `stream` (the handle's stream, as cudaStream_t) after the call may use, or NULL if it
+   * cannot, in which case the call that needed it returns CCSD_ERR_OOM and the handle stays
+   * usable; free(p, stream, alloc_ctx) releases p once the work already queued on `stream`
+   * has finished (the ordering of cudaFreeAsync).  Every block is freed by ccsd_destroy at
+   * the latest.  The callbacks are called from the thread making the library call.  Handles
+   * with callbacks cannot join a batch (ccsd_batch_create returns CCSD_ERR_ARG). */
+  void* (*alloc)(size_t bytes, void* stream, void* alloc_ctx);
+  void (*free)(void* p, void* stream, void* alloc_ctx);
+  void* alloc_ctx;
 } ccsd_options;
 
 /* Fill *opt with defaults (FP64, tol_res 1e-10, tol_eom 1e-7, tol_lin 1e-9, ...). */
@@ -160,6 +173,34 @@ ccsd_status ccsd_coupling_densities(ccsd_handle h, int k, int l, double* D, doub
 /* F[d] = F_kl^x along ndir directions: dh[d][n*n], dB[d][naux*n*n]. */
 ccsd_status ccsd_derivative_coupling(ccsd_handle h, int k, int l, int ndir, const double* dh, const double* dB,
                                      double* F);
+
+/* State-energy gradients (Results section: the crossing-point search needs the gradients
+ * of the two states besides their coupling).  The densities of the energy Lagrangian of
+ * state k, built like the coupling Lagrangian with the state energy in place of the
+ * overlap: for k = 0 (ground state) E + lambda.Omega with lambda^T A = -eta^T; for
+ * k >= 1, E_k = E_0 + omega_k and omega_k = L_k.(A R_k) is stationary in the
+ * biorthonormal L_k, R_k, so E + lambda.Omega + L_k.(A R_k) + zeta.Omega with
+ * zeta^T A = -(F(L_k) R_k)^T (the F-matrix of Eq. for F with gamma = L_k and no reference
+ * part).  With relax_orbitals = 1 kappa-bar^T A^HF = -(k-eta)^T adds kappa-bar_ai F^x_ai
+ * (no overlap term in k-eta).  D[n*n], Z[naux*n*n] (Z may be NULL), host or device.
+ * k = 0 needs ccsd_solve_ground, k >= 1 also both EOM solves (CCSD_ERR_STATE otherwise);
+ * k beyond the solved roots: CCSD_ERR_ARG. */
+ccsd_status ccsd_gradient_densities(ccsd_handle h, int k, double* D, double* Z);
+
+/* g[d] = dE_k/dx along ndir directions dh[d][n*n], dB[d][naux*n*n] (host or device):
+ * sum_pq D_pq dh_pq + sum_Jpq Z_Jpq dB_Jpq with the densities of ccsd_gradient_densities. */
+ccsd_status ccsd_energy_gradient(ccsd_handle h, int k, int ndir, const double* dh, const double* dB, double* g);
+
+/* Branching plane of the excited states k and l (1 <= k, l, k != l) over ndir coordinate
+ * directions taken as orthonormal (Results section, the conical-intersection search):
+ *   out[0..ndir)        g = grad (E_l - E_k)
+ *   out[ndir..2ndir)    h = (E_l - E_k) F_kl  (F_kl of Eq. NAC_NC along each direction)
+ *   out[2ndir..3ndir)   G = P grad E_l + 2 (E_l - E_k) g/|g|, with P the projector onto the
+ *                       complement of span{g, h}: the Bearpark-Robb-Schlegel direction whose
+ *                       zero is a minimum-energy crossing point.
+ * out[3*ndir] host or device memory.  Needs the EOM states (CCSD_ERR_STATE otherwise). */
+ccsd_status ccsd_branching_plane(ccsd_handle h, int k, int l, int ndir, const double* dh, const double* dB,
+                                 double* out);
 
 /* ---- Hartree-Fock orbitals (relaxed mode) -------------------------------------
  * The nearest Hartree-Fock orbitals to the given orthonormal ones: U = exp(K) with
@@ -241,6 +282,21 @@ ccsd_status ccsd_batch_eom_solve(ccsd_batch b, int side, int nroots, double* ome
 ccsd_status ccsd_batch_stats(ccsd_batch b, long long* launches, long long* captures, long long* nodes);
 const char* ccsd_batch_last_error(ccsd_batch b);
 void ccsd_batch_destroy(ccsd_batch b);
+
+/* Budget of every pipeline wait (TMA copy, MMA completion, accumulator hand-off) of the
+ * handle's tensor-core kernels, in GPU clock cycles; 0 restores the default (4e9 cycles,
+ * about 2 s).  A kernel whose wait runs out raises a device flag, waits (with the default
+ * bound) for its own copies and MMAs in flight, releases its tensor memory and exits; the
+ * call that launched it returns CCSD_ERR_TIMEOUT, and the handle stays usable.  The paper
+ * has no counterpart (failure detection of this library).  cycles < 0: CCSD_ERR_ARG. */
+ccsd_status ccsd_set_wait_budget(ccsd_handle h, long long cycles);
+
+/* Failure injection for tests of the timeout path (no counterpart in the paper): the next
+ * split-bf16 tensor-core GEMM the handle launches issues no operand loads, so the waits of
+ * its MMA issuer run out after the wait budget and the call returns CCSD_ERR_TIMEOUT.
+ * Nothing is left in flight, no fault is raised, and later calls run normally.  Only for
+ * CCSD_PREC_MIXED handles (CCSD_ERR_STATE otherwise). */
+ccsd_status ccsd_inject_stall(ccsd_handle h);
 
 /* Allocation-free variant of ccsd_derivative_coupling (the paper has no
  * counterpart; this is a service for callers that cannot allocate device

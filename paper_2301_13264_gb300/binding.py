@@ -21,6 +21,12 @@ PREC_FP64, PREC_MIXED, PREC_FP64_TC = 0, 1, 2
 GEMM_FP64, GEMM_SPLIT, GEMM_FP64_TC = 0, 1, 2
 
 
+# device-allocator callbacks of ccsd_options: alloc(bytes, stream, ctx) -> pointer or NULL,
+# free(pointer, stream, ctx)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class Options(ctypes.Structure):
     _fields_ = [
         ("precision", ctypes.c_int),
@@ -41,6 +47,9 @@ class Options(ctypes.Structure):
         ("tol_switch", ctypes.c_double),
         ("autotune", ctypes.c_int),
         ("fp64_tc", ctypes.c_int),
+        ("alloc", ALLOC_FN),
+        ("free", FREE_FN),
+        ("alloc_ctx", ctypes.c_void_p),
     ]
 
 
@@ -217,6 +226,25 @@ def ccsd_derivative_coupling(h, k, l, ndir, dh, dB):
     return list(F)
 
 
+def ccsd_gradient_densities(h, k, D, Z=None):
+    _check(h, lib().ccsd_gradient_densities(h, k, _ptr(D), _ptr(Z)))
+
+
+def ccsd_energy_gradient(h, k, ndir, dh, dB):
+    g = (ctypes.c_double * ndir)()
+    _check(h, lib().ccsd_energy_gradient(h, k, ndir, _ptr(dh), _ptr(dB), g))
+    return list(g)
+
+
+def ccsd_branching_plane(h, k, l, ndir, dh, dB):
+    """(g, h, G) as three lists of ndir values: grad(E_l - E_k), (E_l - E_k) F_kl and the
+    Bearpark-Robb-Schlegel direction."""
+    out = (ctypes.c_double * (3 * ndir))()
+    _check(h, lib().ccsd_branching_plane(h, k, l, ndir, _ptr(dh), _ptr(dB), out))
+    v = list(out)
+    return v[:ndir], v[ndir:2 * ndir], v[2 * ndir:]
+
+
 def ccsd_derivative_coupling_noalloc(h, k, l, ndir, dh, dB):
     """Allocation-free variant; dh and dB must be device tensors, densities held."""
     F = (ctypes.c_double * ndir)()
@@ -256,6 +284,18 @@ def ccsd_gemm(form, A, B, C=None, alpha=1.0, beta=0.0, splits=3, reps=1):
     _check(None, L.ccsd_gemm(form, splits, M, N, K, alpha, _ptr(A), _ptr(B), beta, _ptr(C), reps,
                              ctypes.byref(ms)))
     return C, ms.value
+
+
+def ccsd_set_wait_budget(h, cycles: int):
+    """Budget of each tensor-core pipeline wait in GPU clock cycles (0: the default)."""
+    L = lib()
+    L.ccsd_set_wait_budget.argtypes = [_P, ctypes.c_longlong]
+    _check(h, L.ccsd_set_wait_budget(h, int(cycles)))
+
+
+def ccsd_inject_stall(h):
+    """Test hook: the handle's next split-bf16 tensor-core GEMM issues no loads and times out."""
+    _check(h, lib().ccsd_inject_stall(h))
 
 
 def ccsd_profile_start(h):

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/ccsd.h"
+#include "alloc.h"
 #include "exec.h"
 #include "kernels.cuh"
 #include "mlp.h"
@@ -61,13 +62,15 @@ struct DevBuf {
   int64_t n = 0;
   DevBuf() = default;
   explicit DevBuf(int64_t n_) { alloc(n_); }
+  // device memory of the handle whose call is running (its allocator callbacks, else
+  // cudaMalloc); released on the handle's stream in the callbacks' case
   void alloc(int64_t n_) {
     release();
+    p = (double*)dev_alloc(std::max<int64_t>(n_, 1) * sizeof(double), active_stream(), false);
     n = n_;
-    CUDA_OK(cudaMalloc(&p, std::max<int64_t>(n, 1) * sizeof(double)));
   }
   void release() {
-    if (p) cudaFree(p);
+    dev_free(p, active_stream(), false);
     p = nullptr;
     n = 0;
   }
@@ -85,6 +88,7 @@ struct ccsd_ctx {
   int64_t dim = 0, n1 = 0;
   cudaStream_t st = 0;
   int device = 0;  // the GPU that was current at ccsd_create: all of the handle's memory lives there
+  DeviceAllocator allocator;  // the caller's allocator callbacks (none: the CUDA runtime)
   Programs P;
   std::unique_ptr<Executor> ex;
   DevBuf eps, h, B, ones;
@@ -870,13 +874,17 @@ ccsd_status fail(ccsd_ctx* c, ccsd_status s, const std::string& msg) {
 template <typename F>
 ccsd_status guarded(ccsd_ctx* c, F&& f) {
   if (!c) return CCSD_ERR_ARG;
+  AllocatorScope scope(&c->allocator, c->st);
   try {
+    TempScope temps;  // released if f() throws
     f();
     return CCSD_OK;
   } catch (const Err& e) {
     return fail(c, e.code, e.what());
   } catch (const DeviceTimeout& e) {
     return fail(c, CCSD_ERR_TIMEOUT, e.what());
+  } catch (const OutOfMemory& e) {
+    return fail(c, CCSD_ERR_OOM, e.what());
   } catch (const std::bad_alloc& e) {
     return fail(c, CCSD_ERR_OOM, "host allocation failed");
   } catch (const std::exception& e) {
@@ -1135,12 +1143,17 @@ void transition_density(ccsd_ctx* c, int k, int l, double* D) {
 // With the condition densities of the pair in Dd, Zd: k-eta, kappa-bar, and the
 // kappa-bar densities added to Dd, Zd (so that the coupling contraction carries
 // kappa-bar_ai F^q_ai).
-void add_orbital_relaxation(ccsd_ctx* c, int k, int l) {
+// overlap = false (state-energy gradients): the Lagrangian has no overlap term, so k-eta is
+// the condition part alone.
+void add_orbital_relaxation(ccsd_ctx* c, int k, int l, bool overlap = true) {
   const int o = c->o, v = c->v, n = c->n;
   const int64_t nn = (int64_t)n * n, nz = (int64_t)c->naux * nn, m = (int64_t)o * v;
   PrecScope fp64(c, fp64_prec(c));
   DevBuf Dt(nn);
-  transition_density(c, k, l, Dt.p);
+  if (overlap)
+    transition_density(c, k, l, Dt.p);
+  else
+    CUDA_OK(cudaMemsetAsync(Dt.p, 0, nn * sizeof(double), c->st));
   Executor& hx = hf_exec(c);
   const HFPrograms& P = *c->hfp;
   // condition part of k-eta: the adjoint of the rotation map applied to (D, Z)
@@ -1244,6 +1257,113 @@ void compute_densities(ccsd_ctx* c, int k, int l) {
   c->dens_l = l;
 }
 
+// dens_l value marking that Dd, Zd hold the state-energy gradient densities of state dens_k
+constexpr int kGradientDensities = -2;
+
+// Densities D = dL/dh, Z = dL/dB of the energy Lagrangian of state k at the solved
+// amplitudes and multipliers (the Lagrangian construction of the paper with the state
+// energy in place of the overlap):
+//   k = 0:  L = E + lambda.Omega                         (lambda^T A = -eta^T)
+//   k >= 1: L = E + lambda.Omega + L_k.(A R_k) + zeta.Omega, zeta^T A = -(F(L_k) R_k)^T,
+// since E_k = E_0 + omega_k and omega_k = L_k.(A R_k) is stationary in the biorthonormal
+// L_k, R_k (L_k.R_k = 1, l_0 = 0), so only its amplitude dependence needs a multiplier.
+// Relaxed orbitals add kappa-bar from kappa-bar^T A^HF = -k-eta^T (no overlap term).
+void compute_gradient_densities(ccsd_ctx* c, int k) {
+  const int nr = (int)c->omega.size();
+  if (k < 0 || k > nr) throw Err(CCSD_ERR_ARG, "state index beyond the solved roots");
+  if (!c->have_ground) throw Err(CCSD_ERR_STATE, "ground state not solved");
+  if (k > 0 && !(c->have_right && c->have_left)) throw Err(CCSD_ERR_STATE, "EOM states not solved");
+  if (c->dens_k == k && c->dens_l == kGradientDensities) return;
+  c->dens_k = c->dens_l = -1;
+  ensure_cache(c);
+  const int64_t dim = c->dim, nn = (int64_t)c->n * c->n, nz = (int64_t)c->naux * nn;
+  auto& P = c->P;
+  Executor& ex = *c->ex;
+  if (!c->Dd.p) c->Dd.alloc(nn);
+  if (!c->Zd.p) c->Zd.alloc(nz);
+  // E + lambda.Omega
+  {
+    DevBuf Wl(dim), e1(1);
+    const double one = 1.0;
+    launch_weight(c->vs, c->lam.p, Wl.p, 1, dim, c->st);
+    CUDA_OK(cudaMemcpyAsync(e1.p, &one, sizeof(double), cudaMemcpyHostToDevice, c->st));
+    ex.set_nvec(1);
+    ex.bind(P.eZ1, Wl.p);
+    ex.bind(P.eZ2, Wl.p + c->n1);
+    ex.bind(P.eE, e1.p);
+    ex.bind(P.eH, c->Dd.p);
+    ex.bind(P.eB, c->Zd.p);
+    PrecScope p(c, refining(c) ? fp64_prec(c) : ex.precision());
+    ex.run(P.dens0);
+    sync(c);
+  }
+  if (k > 0) {
+    const double* Lk = c->L[k - 1]->p;
+    const double* Rk = c->R[k - 1]->p;
+    DevBuf hv(dim), zeta(dim), Wz(dim), WL(dim), s0(1), D2(nn), Z2(nz);
+    {
+      PrecScope p(c, refining(c) ? fp64_prec(c) : ex.precision());
+      hess_right(c, 0.0, Lk, Rk, hv.p);
+    }
+    // zeta^T A = -(F(L_k) R_k)^T
+    launch_precond(c->vs, c->eps.p, hv.p, zeta.p, 0.0, c->st);
+    launch_axpby(dim, 0.0, zeta.p, -1.0, zeta.p, c->st);
+    solve_left_refined(c, hv.p, zeta.p, c->opt.tol_lin);
+    launch_weight(c->vs, zeta.p, Wz.p, 1, dim, c->st);
+    launch_weight(c->vs, Lk, WL.p, 1, dim, c->st);
+    CUDA_OK(cudaMemsetAsync(s0.p, 0, sizeof(double), c->st));
+    ensure_cache(c);
+    ex.set_nvec(1);
+    ex.bind(P.dZ1, Wz.p);
+    ex.bind(P.dZ2, Wz.p + c->n1);
+    ex.bind(P.dG1, WL.p);
+    ex.bind(P.dG2, WL.p + c->n1);
+    ex.bind(P.dG0, s0.p);
+    ex.bind(P.dR1, const_cast<double*>(Rk));
+    ex.bind(P.dR2, const_cast<double*>(Rk) + c->n1);
+    ex.bind(P.dH, D2.p);
+    ex.bind(P.dB, Z2.p);
+    {
+      PrecScope p(c, refining(c) ? fp64_prec(c) : ex.precision());
+      ex.run(P.dens1);
+    }
+    launch_axpby(nn, 1.0, D2.p, 1.0, c->Dd.p, c->st);
+    launch_axpby(nz, 1.0, Z2.p, 1.0, c->Zd.p, c->st);
+    sync(c);
+  }
+  if (c->opt.relax_orbitals) add_orbital_relaxation(c, k, k, false);
+  c->dens_k = k;
+  c->dens_l = kGradientDensities;
+}
+
+// F[d] = <Dd, dh[d]> + <Zd, dB[d]> for the densities the handle holds (host or device directions)
+void contract_densities(ccsd_ctx* c, int ndir, const double* dh, const double* dB, double* F) {
+  const int64_t nn = (int64_t)c->n * c->n, nb = (int64_t)c->naux * nn;
+  DevBuf out(2), tmp;
+  bool hdev = is_device_ptr(dh), bdev = is_device_ptr(dB);
+  double* work = c->ex->scratch(1024);
+  for (int d = 0; d < ndir; ++d) {
+    double fh, fb;
+    const double* hp = dh + d * nn;
+    if (!hdev) {
+      to_device(c, hp, nn, tmp);
+      hp = tmp.p;
+    }
+    launch_dot(nn, c->Dd.p, hp, out.p, work, c->st);
+    CUDA_OK(cudaMemcpyAsync(&fh, out.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    sync(c);
+    const double* bp = dB + d * nb;
+    if (!bdev) {
+      to_device(c, bp, nb, tmp);
+      bp = tmp.p;
+    }
+    launch_dot(nb, c->Zd.p, bp, out.p, work, c->st);
+    CUDA_OK(cudaMemcpyAsync(&fb, out.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    sync(c);
+    F[d] = fh + fb;
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -1303,6 +1423,14 @@ ccsd_status ccsd_create(const double* eps, const double* h, const double* B, int
     c->opt = *opt;
   else
     ccsd_default_options(&c->opt);
+  if ((c->opt.alloc != nullptr) != (c->opt.free != nullptr)) {
+    delete c;
+    return CCSD_ERR_ARG;
+  }
+  c->allocator.alloc = c->opt.alloc;
+  c->allocator.free = c->opt.free;
+  c->allocator.ctx = c->opt.alloc_ctx;
+  c->st = (cudaStream_t)c->opt.stream;
   if ((c->opt.relax_orbitals != 0 && c->opt.relax_orbitals != 1) ||
       (c->opt.precision != CCSD_PREC_FP64 && c->opt.precision != CCSD_PREC_MIXED &&
        c->opt.precision != CCSD_PREC_FP64_TC)) {
@@ -1405,6 +1533,7 @@ void ccsd_destroy(ccsd_handle h) {
   if (!h) return;
   if (h->st) cudaStreamSynchronize(h->st);
   else cudaDeviceSynchronize();
+  AllocatorScope scope(&h->allocator, h->st);  // the handle's memory goes back to its allocator
   delete h;
 }
 
@@ -1623,30 +1752,49 @@ ccsd_status ccsd_derivative_coupling(ccsd_handle c, int k, int l, int ndir, cons
   return guarded(c, [&] {
     if (ndir < 1 || !dh || !dB || !F) throw Err(CCSD_ERR_ARG, "bad arguments");
     compute_densities(c, k, l);
-    const int64_t nn = (int64_t)c->n * c->n, nb = (int64_t)c->naux * nn;
-    DevBuf out(2), tmp;
-    bool hdev = is_device_ptr(dh), bdev = is_device_ptr(dB);
-    double* work = c->ex->scratch(1024);
-    for (int d = 0; d < ndir; ++d) {
-      double fh, fb;
-      const double* hp = dh + d * nn;
-      if (!hdev) {
-        to_device(c, hp, nn, tmp);
-        hp = tmp.p;
-      }
-      launch_dot(nn, c->Dd.p, hp, out.p, work, c->st);
-      CUDA_OK(cudaMemcpyAsync(&fh, out.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
-      sync(c);
-      const double* bp = dB + d * nb;
-      if (!bdev) {
-        to_device(c, bp, nb, tmp);
-        bp = tmp.p;
-      }
-      launch_dot(nb, c->Zd.p, bp, out.p, work, c->st);
-      CUDA_OK(cudaMemcpyAsync(&fb, out.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
-      sync(c);
-      F[d] = fh + fb;
-    }
+    contract_densities(c, ndir, dh, dB, F);
+  });
+}
+
+ccsd_status ccsd_gradient_densities(ccsd_handle c, int k, double* D, double* Z) {
+  return guarded(c, [&] {
+    if (!D) throw Err(CCSD_ERR_ARG, "null pointer");
+    compute_gradient_densities(c, k);
+    const int64_t nn = (int64_t)c->n * c->n;
+    from_device(c, c->Dd.p, nn, D);
+    if (Z) from_device(c, c->Zd.p, (int64_t)c->naux * nn, Z);
+    sync(c);
+  });
+}
+
+ccsd_status ccsd_energy_gradient(ccsd_handle c, int k, int ndir, const double* dh, const double* dB, double* g) {
+  return guarded(c, [&] {
+    if (ndir < 1 || !dh || !dB || !g) throw Err(CCSD_ERR_ARG, "bad arguments");
+    compute_gradient_densities(c, k);
+    contract_densities(c, ndir, dh, dB, g);
+  });
+}
+
+ccsd_status ccsd_branching_plane(ccsd_handle c, int k, int l, int ndir, const double* dh, const double* dB,
+                                 double* out) {
+  return guarded(c, [&] {
+    if (ndir < 1 || !dh || !dB || !out) throw Err(CCSD_ERR_ARG, "bad arguments");
+    if (k < 1 || l < 1 || k == l) throw Err(CCSD_ERR_ARG, "branching plane of two distinct excited states");
+    std::vector<double> gk(ndir), gl(ndir), f(ndir);
+    compute_gradient_densities(c, k);
+    contract_densities(c, ndir, dh, dB, gk.data());
+    compute_gradient_densities(c, l);
+    contract_densities(c, ndir, dh, dB, gl.data());
+    compute_densities(c, k, l);
+    contract_densities(c, ndir, dh, dB, f.data());
+    const double gap = omega_of(c, l) - omega_of(c, k);  // E_l - E_k
+    DevBuf d(6 * (int64_t)ndir);
+    CUDA_OK(cudaMemcpyAsync(d.p, gk.data(), ndir * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CUDA_OK(cudaMemcpyAsync(d.p + ndir, gl.data(), ndir * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CUDA_OK(cudaMemcpyAsync(d.p + 2 * ndir, f.data(), ndir * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    launch_branching_plane(ndir, gap, d.p, d.p + ndir, d.p + 2 * ndir, d.p + 3 * ndir, c->st);
+    from_device(c, d.p + 3 * ndir, 3 * (int64_t)ndir, out);
+    sync(c);
   });
 }
 
@@ -1690,6 +1838,9 @@ ccsd_status unguarded(F&& f) {
   } catch (const Err& e) {
     g_last_error = e.what();
     return e.code;
+  } catch (const OutOfMemory& e) {
+    g_last_error = e.what();
+    return CCSD_ERR_OOM;
   } catch (const std::bad_alloc&) {
     g_last_error = "host allocation failed";
     return CCSD_ERR_OOM;
@@ -1825,6 +1976,21 @@ ccsd_status ccsd_set_guess_model(ccsd_handle c, const float* model) {
   });
 }
 
+ccsd_status ccsd_set_wait_budget(ccsd_handle c, long long cycles) {
+  return guarded(c, [&] {
+    if (cycles < 0) throw Err(CCSD_ERR_ARG, "wait budget must be >= 0");
+    c->ex->wait_cycles = cycles;
+    if (c->hx) c->hx->wait_cycles = cycles;
+  });
+}
+
+ccsd_status ccsd_inject_stall(ccsd_handle c) {
+  return guarded(c, [&] {
+    if (c->opt.precision != CCSD_PREC_MIXED) throw Err(CCSD_ERR_STATE, "stall injection needs a mixed-precision handle");
+    c->ex->stall_next = true;
+  });
+}
+
 ccsd_status ccsd_profile_start(ccsd_handle c) {
   return guarded(c, [&] {
     c->ex->collect();
@@ -1933,6 +2099,9 @@ ccsd_status batch_guarded(ccsd_batch_ctx* b, F&& f) {
   } catch (const DeviceTimeout& e) {
     b->err = e.what();
     return CCSD_ERR_TIMEOUT;
+  } catch (const OutOfMemory& e) {
+    b->err = e.what();
+    return CCSD_ERR_OOM;
   } catch (const std::bad_alloc&) {
     b->err = "host allocation failed";
     return CCSD_ERR_OOM;
@@ -2093,7 +2262,9 @@ ccsd_status ccsd_batch_create(int nsys, const ccsd_handle* systems, int nvec, cc
   *out = nullptr;
   if (nsys < 1 || !systems || nvec < 1 || nvec > 16) return CCSD_ERR_ARG;
   for (int s = 0; s < nsys; ++s) {
-    if (!systems[s]) return CCSD_ERR_ARG;
+    // a batch captures its systems' work into CUDA graphs, whose temporaries are graph
+    // memory nodes: systems with allocator callbacks cannot take part
+    if (!systems[s] || systems[s]->allocator.custom()) return CCSD_ERR_ARG;
     for (int r = 0; r < s; ++r)
       if (systems[r] == systems[s]) return CCSD_ERR_ARG;
   }

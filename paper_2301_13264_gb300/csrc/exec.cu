@@ -1,10 +1,13 @@
 // Program executor: label analysis, operand gathering, GEMM dispatch.
 #include "exec.h"
 
+#include "alloc.h"
+
 #include <algorithm>
 #include <map>
 #include <cstdio>
 #include <cstdlib>
+#include <exception>
 #include <stdexcept>
 
 namespace ccsd {
@@ -23,8 +26,8 @@ Executor::Executor(const Graph& g, int o, int v, int naux, int nvec_max, cudaStr
 Executor::~Executor() {
   clear_cache();
   for (auto& t : ts_)
-    if (t.owned && t.p) cudaFree(t.p);
-  if (scratch_) cudaFree(scratch_);
+    if (t.owned && t.p) dev_free(t.p, st_, false);
+  dev_free(scratch_, st_, false);
 }
 
 void Executor::set_nvec(int nvec) {
@@ -51,7 +54,7 @@ int64_t Executor::numel(int t) const {
 
 void Executor::bind(int t, double* p, int64_t zstride) {
   TS& s = ts_[t];
-  if (s.owned && s.p) CK(cudaFree(s.p));
+  if (s.owned && s.p) dev_free(s.p, st_, false);
   s.p = p;
   s.owned = false;
   s.bound = true;
@@ -72,28 +75,27 @@ void Executor::alloc_persistent(int t) {
   if (s.p) return;
   int64_t n = 1;
   for (char c : g_.T[t].cls) n *= (c == 'z') ? nvec_max_ : extent(c);
-  CK(cudaMalloc(&s.p, std::max<int64_t>(n, 1) * sizeof(double)));
+  s.p = (double*)dev_alloc(std::max<int64_t>(n, 1) * sizeof(double), st_, false);
   CK(cudaMemsetAsync(s.p, 0, std::max<int64_t>(n, 1) * sizeof(double), st_));
   s.owned = true;
 }
 
 double* Executor::scratch(int64_t n) {
   if (n > scratch_n_) {
-    if (scratch_) CK(cudaFree(scratch_));
-    CK(cudaMalloc(&scratch_, n * sizeof(double)));
+    dev_free(scratch_, st_, false);
+    scratch_ = nullptr;
+    scratch_ = (double*)dev_alloc(n * sizeof(double), st_, false);
     scratch_n_ = n;
   }
   return scratch_;
 }
 
 double* Executor::tmp_alloc(int64_t n) {
-  void* p = nullptr;
-  CK(cudaMallocAsync(&p, std::max<int64_t>(n, 1) * sizeof(double), st_));
-  return (double*)p;
+  return (double*)dev_alloc(std::max<int64_t>(n, 1) * sizeof(double), st_, true);
 }
 
 void Executor::tmp_free(double* p) {
-  if (p) CK(cudaFreeAsync(p, st_));
+  dev_free(p, st_, true);
 }
 
 Executor::SView Executor::resolve(const Ref& r) const {
@@ -534,6 +536,17 @@ void Executor::run(const Prog& p) {
     CK(cudaEventCreate(&ev0));
     CK(cudaEventCreate(&ev1));
   }
+  // a run that ends by an exception leaves no temporary bound: the call's TempScope
+  // releases their memory, and the next run must allocate them afresh
+  struct ResetTemps {
+    std::vector<TS>& ts;
+    const std::set<int>& temps;
+    int uncaught = std::uncaught_exceptions();
+    ~ResetTemps() {
+      if (std::uncaught_exceptions() > uncaught)
+        for (int t : temps) ts[t].p = nullptr;
+    }
+  } reset_temps{ts_, run_temps};
   for (int i = 0; i < (int)p.size(); ++i) {
     const Op& op = p[i];
     if (op_timing) CK(cudaEventRecord(ev0, st_));

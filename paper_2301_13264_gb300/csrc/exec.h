@@ -65,6 +65,12 @@ class Executor {
   int autotune = 0;
   // contractions with fewer flops than this stay on the FP64 path in mixed mode
   double tc_min_flops = 2.0e9;
+  // clock cycles a pipeline wait of a tensor-core kernel may take before the kernel
+  // raises the error flag and exits (0: the default bound, about 2 s)
+  long long wait_cycles = 0;
+  // failure injection for tests: the next tensor-core GEMM launch issues no operand
+  // loads, so its waits run out after wait_cycles (cleared by that launch)
+  bool stall_next = false;
   ExecStats stats;
   cudaStream_t stream() const { return st_; }
   // device scratch for reductions

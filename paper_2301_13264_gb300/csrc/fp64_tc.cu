@@ -43,6 +43,7 @@
 // blockIdx.z writes FP64 partial tiles that a second kernel sums.  Every wait is
 // bounded; on timeout the kernel raises the error flag, drains its own copies and
 // MMAs (bounded), frees TMEM and exits.
+#include "alloc.h"
 #include "fp64_tc.h"
 
 #include <cuda.h>
@@ -85,6 +86,8 @@ struct Params {
   int* err;
   int ostr;
   Strided om, on;
+  long long budget;  // clock cycles a pipeline wait may take before the kernel gives up
+  int mt, nt, group_m;  // output tiles (rows, columns) and rows per raster group (tc::raster_tile)
 };
 
 __device__ __forceinline__ long long dim_off(long long x, const Strided& g) {
@@ -160,7 +163,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const uint32_t accfull = tc::smem_u32(bars + 12), accempty = tc::smem_u32(bars + 13);
   const uint32_t done = tc::smem_u32(bars + 14);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  int tm, tn;
+  tc::raster_tile(blockIdx.x, p.mt, p.nt, p.group_m, tm, tn);
+  const int m0 = tm * BM, n0 = tn * BN;
   const int kt0 = blockIdx.z * p.kt_per_split;
   const int nkt = max(0, min(p.kt_total, kt0 + p.kt_per_split) - kt0);
   const int nch = (nkt + KC_TILES - 1) / KC_TILES;
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool ok = true;
       for (int k = 0; k < nkt && ok; ++k) {
         const int bs = k % B_STAGES;
-        if (!tc::mbar_wait(bempty + 8 * bs, ((uint32_t)(k / B_STAGES) & 1u) ^ 1u, err)) {
+        if (!tc::mbar_wait(bempty + 8 * bs, ((uint32_t)(k / B_STAGES) & 1u) ^ 1u, err, p.budget)) {
           ok = false;
           break;
         }
@@ -210,7 +215,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         ++nb;
         for (int s = 0; s < S; ++s) {
           const int as = na % A_STAGES;
-          if (!tc::mbar_wait(aempty + 8 * as, ((uint32_t)(na / A_STAGES) & 1u) ^ 1u, err)) {
+          if (!tc::mbar_wait(aempty + 8 * as, ((uint32_t)(na / A_STAGES) & 1u) ^ 1u, err, p.budget)) {
             ok = false;
             break;
           }
@@ -238,21 +243,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         const int kc = k % KC_TILES, ch = k / KC_TILES;
         if (kc == 0 && ch > 0) {
           // the previous chunk's accumulators must have been read out
-          if (!tc::mbar_wait(accempty, (uint32_t)(ch - 1) & 1u, err)) {
+          if (!tc::mbar_wait(accempty, (uint32_t)(ch - 1) & 1u, err, p.budget)) {
             ok = false;
             break;
           }
           tc::fence_after();
         }
         const int bs = k % B_STAGES;
-        if (!tc::mbar_wait(bfull + 8 * bs, (uint32_t)(k / B_STAGES) & 1u, err)) {
+        if (!tc::mbar_wait(bfull + 8 * bs, (uint32_t)(k / B_STAGES) & 1u, err, p.budget)) {
           ok = false;
           break;
         }
         tc::fence_after();
         for (int s = 0; s < S; ++s) {
           const int as = na % A_STAGES;
-          if (!tc::mbar_wait(afull + 8 * as, (uint32_t)(na / A_STAGES) & 1u, err)) {
+          if (!tc::mbar_wait(afull + 8 * as, (uint32_t)(na / A_STAGES) & 1u, err, p.budget)) {
             ok = false;
             break;
           }
@@ -292,7 +297,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int j = 0; j < HALF; ++j) acc[j] = 0;
     bool ok = true;
     for (int ch = 0; ch < nch; ++ch) {
-      if (!tc::mbar_wait(accfull, (uint32_t)ch & 1u, err)) {
+      if (!tc::mbar_wait(accfull, (uint32_t)ch & 1u, err, p.budget)) {
         ok = false;
         break;
       }
@@ -444,7 +449,7 @@ void pack(cudaStream_t st, const double* src, const Strided& g, int64_t rows, in
 
 double gemm(cudaStream_t st, const void* a, int64_t Mp, const void* b, int64_t Np, int64_t Kp, int M, int N,
             double* C, int64_t sCm, int64_t sCn, double alpha, double beta, const Strided* om, const Strided* on,
-            int nsplit_req, int* err) {
+            int nsplit_req, int* err, long long budget) {
   if (Mp % BM != 0 || Np % BN != 0 || Kp % BK != 0 || M < 1 || N < 1 || M > Mp || N > Np || Np / BN > 65535)
     throw std::runtime_error("oz::gemm: bad padding");
   if (beta != 0.0 && beta != 1.0) throw std::runtime_error("oz::gemm: beta must be 0 or 1");
@@ -482,6 +487,7 @@ double gemm(cudaStream_t st, const void* a, int64_t Mp, const void* b, int64_t N
   p.alpha = alpha;
   p.beta_zero = (beta == 0.0) ? 1 : 0;
   p.err = err;
+  p.budget = budget;
   p.ostr = (om && on) ? 1 : 0;
   if (p.ostr) {
     p.om = *om;
@@ -489,16 +495,18 @@ double gemm(cudaStream_t st, const void* a, int64_t Mp, const void* b, int64_t N
   } else {
     p.om.ndim = p.on.ndim = 0;
   }
-  if (nsplit > 1 &&
-      cudaMallocAsync((void**)&p.part, (size_t)nsplit * M * N * sizeof(double), st) != cudaSuccess)
-    throw std::runtime_error("oz::gemm split workspace allocation failed");
-  dim3 grid((unsigned)(Mp / BM), (unsigned)(Np / BN), (unsigned)nsplit);
+  if (nsplit > 1) p.part = (double*)dev_alloc((size_t)nsplit * M * N * sizeof(double), st, true);
+  if ((Mp / BM) * (Np / BN) > (int64_t)INT32_MAX) throw std::runtime_error("oz::gemm: too many tiles");
+  p.mt = (int)(Mp / BM);
+  p.nt = (int)(Np / BN);
+  p.group_m = tc::raster_group(p.mt, BN);
+  dim3 grid((unsigned)(p.mt * p.nt), 1u, (unsigned)nsplit);
   count_launches(1);
   k_tc_dgemm<<<grid, NTHREADS, SMEM_BYTES, st>>>(ta, tb, p);
   if (nsplit > 1) {
     launch_split_reduce_fp64(M, N, nsplit, p.part, C, sCm, sCn, p.beta_zero, p.ostr ? om : nullptr,
                              p.ostr ? on : nullptr, st);
-    cudaFreeAsync(p.part, st);
+    dev_free(p.part, st, true);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw std::runtime_error(std::string("oz::gemm launch: ") + cudaGetErrorString(e));

@@ -35,7 +35,7 @@ void pack(cudaStream_t st, const double* src, const Strided& g, int64_t rows, in
 // err: device flag raised when a wait of the kernel times out.  Returns the MMA flops issued.
 double gemm(cudaStream_t st, const void* a, int64_t Mp, const void* b, int64_t Np, int64_t Kp, int M, int N,
             double* C, int64_t sCm, int64_t sCn, double alpha, double beta, const Strided* om, const Strided* on,
-            int nsplit, int* err);
+            int nsplit, int* err, long long budget);
 
 }  // namespace oz
 

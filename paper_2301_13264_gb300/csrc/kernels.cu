@@ -2,6 +2,8 @@
 // operations (packed inner products, preconditioner, pair symmetrisation).
 #include "kernels.cuh"
 
+#include "alloc.h"
+
 #include <algorithm>
 #include <atomic>
 #include <stdexcept>
@@ -408,14 +410,13 @@ static void launch_dgemm_chunk(const GemmArgs& g, cudaStream_t st) {
     int64_t nsplit = std::min<int64_t>(std::max<int64_t>(1, target / (outputs * g.batch)), (g.K + 2047) / 2048);
     nsplit = std::max<int64_t>(nsplit, 1);
     int64_t kchunk = (g.K + nsplit - 1) / nsplit;
-    double* part = nullptr;
     size_t bytes = (size_t)nsplit * g.batch * outputs * sizeof(double);
-    if (cudaMallocAsync((void**)&part, bytes, st) != cudaSuccess) throw std::runtime_error("dgemm: workspace");
+    double* part = (double*)dev_alloc(bytes, st, true);
     dim3 grid((unsigned)nsplit, (unsigned)outputs, g.batch);
     count_launches(2);
     k_ddot_split<<<grid, 256, 0, st>>>(g, (int)nsplit, kchunk, part);
     k_split_reduce<<<grid_for(g.batch * outputs), 256, 0, st>>>(g, (int)nsplit, part);
-    cudaFreeAsync(part, st);
+    dev_free(part, st, true);
     return;
   }
   const int64_t tm = (g.M + DT - 1) / DT, tn = (g.N + DT - 1) / DT;
@@ -436,14 +437,13 @@ static void launch_dgemm_chunk(const GemmArgs& g, cudaStream_t st) {
   int kchunk = (g.K + nsplit - 1) / nsplit;
   kchunk = (kchunk + DK - 1) / DK * DK;
   nsplit = (g.K + kchunk - 1) / kchunk;
-  double* part = nullptr;
   size_t bytes = (size_t)nsplit * g.batch * g.M * g.N * sizeof(double);
-  if (cudaMallocAsync((void**)&part, bytes, st) != cudaSuccess) throw std::runtime_error("dgemm: workspace");
+  double* part = (double*)dev_alloc(bytes, st, true);
   dim3 grid((unsigned)tn, (unsigned)tm, (unsigned)(g.batch * nsplit));
   count_launches(2);
   k_dgemm<<<grid, 256, 0, st>>>(g, nsplit, kchunk, part);
   k_split_reduce<<<grid_for((int64_t)g.batch * g.M * g.N), 256, 0, st>>>(g, nsplit, part);
-  cudaFreeAsync(part, st);
+  dev_free(part, st, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -816,4 +816,74 @@ void launch_tau_expectation(const VecShape& s, double r0, const double* L, const
   k_axpby<<<grid_for(n2), 256, 0, st>>>(n2, r0, L + s.n1(), 0.0, y + s.n1());
 }
 
+}  // namespace ccsd
+
+namespace ccsd {
+namespace {
+// block-wide sum of one value per thread (blockDim.x a multiple of 32, at most 1024)
+__device__ double block_sum(double x, double* red) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = x;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t += red[i];
+  return t;
+}
+
+__global__ void k_branching_plane(int n, double gap, const double* __restrict__ gk, const double* __restrict__ gl,
+                                  const double* __restrict__ f, double* __restrict__ out) {
+  __shared__ double red[32];
+  double* g = out;
+  double* h = out + n;
+  double* G = out + 2 * n;
+  double gg = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double gi = gl[i] - gk[i];
+    g[i] = gi;
+    h[i] = gap * f[i];
+    gg += gi * gi;
+  }
+  const double gnorm = sqrt(block_sum(gg, red));
+  const double inv_g = gnorm > 0.0 ? 1.0 / gnorm : 0.0;
+  // h with its component along q1 = g/|g| removed
+  double hq = 0.0, hh = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    hq += h[i] * g[i] * inv_g;
+    hh += h[i] * h[i];
+  }
+  hq = block_sum(hq, red);
+  const double hnorm = sqrt(block_sum(hh, red));
+  double pp = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double hp = h[i] - hq * g[i] * inv_g;
+    pp += hp * hp;
+  }
+  const double pnorm = sqrt(block_sum(pp, red));
+  const bool two = pnorm > 1e-12 * fmax(hnorm, 1e-300);
+  const double inv_p = two ? 1.0 / pnorm : 0.0;
+  // projections of gl on q1 and q2
+  double a1 = 0.0, a2 = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double q1 = g[i] * inv_g;
+    const double q2 = (h[i] - hq * q1) * inv_p;
+    a1 += gl[i] * q1;
+    a2 += gl[i] * q2;
+  }
+  a1 = block_sum(a1, red);
+  a2 = block_sum(a2, red);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double q1 = g[i] * inv_g;
+    const double q2 = (h[i] - hq * q1) * inv_p;
+    G[i] = gl[i] - a1 * q1 - a2 * q2 + 2.0 * gap * q1;
+  }
+}
+}  // namespace
+
+void launch_branching_plane(int n, double gap, const double* gk, const double* gl, const double* f, double* out,
+                            cudaStream_t st) {
+  count_launches(1);
+  k_branching_plane<<<1, 256, 0, st>>>(n, gap, gk, gl, f, out);
+}
 }  // namespace ccsd

@@ -81,6 +81,14 @@ void launch_argmaxabs(int64_t n, const double* x, double* out, double* work, cud
 // t-eta first term: <L|tau_sigma|(r0 + R)> for all packed sigma (see capi.cpp).
 void launch_tau_expectation(const VecShape& s, double r0, const double* L, const double* R, double* y,
                             cudaStream_t st);
+// Branching plane of two states k < l from their energy gradients gk, gl and the coupling
+// f = F_kl along n directions, gap = E_l - E_k (one CTA, FP64):
+//   out[0..n)   g = gl - gk
+//   out[n..2n)  h = gap * f
+//   out[2n..3n) G = P gl + 2 gap g/|g|, P the projector onto the complement of span{g, h}
+// (the crossing-point direction of Bearpark, Robb and Schlegel).  out must not overlap the inputs.
+void launch_branching_plane(int n, double gap, const double* gk, const double* gl, const double* f, double* out,
+                            cudaStream_t st);
 // out[0] = sum_k x[k] y[k] over n elements (plain dot), two-pass via work (>= 1024 doubles).
 void launch_dot(int64_t n, const double* x, const double* y, double* out, double* work, cudaStream_t st);
 

@@ -34,6 +34,7 @@
 #include <string>
 #include <vector>
 
+#include "alloc.h"
 #include "exec.h"
 
 namespace ccsd {
@@ -206,7 +207,7 @@ int grid_of(int64_t n) {
 const int2* Executor::pair_table() {
   if (!pairs_) {
     const int np = v_ * (v_ + 1) / 2;
-    if (cudaMalloc(&pairs_, np * sizeof(int2)) != cudaSuccess) throw std::runtime_error("pair table allocation");
+    pairs_ = dev_alloc(np * sizeof(int2), st_, false);
     count_launches(1);
     k_pair_table<<<(v_ + 127) / 128, 128, 0, st_>>>(v_, (int2*)pairs_);
   }
@@ -325,8 +326,7 @@ bool Executor::try_ladder(const Op& op) {
       if (t.offA == offA && t.offIJ == offIJ && t.offJI == offJI && t.same == same) tab = &t;
     if (!tab) {
       LadderTables t{offA, offIJ, offJI, same, nullptr};
-      if (cudaMalloc(&t.dev, 3 * n8 + same.size() + 16) != cudaSuccess)
-        throw std::runtime_error("ladder row tables: out of memory");
+      t.dev = dev_alloc(3 * n8 + same.size() + 16, st_, false);
       char* base = (char*)t.dev;
       cudaMemcpy(base, offA.data(), n8, cudaMemcpyHostToDevice);
       cudaMemcpy(base + n8, offIJ.data(), n8, cudaMemcpyHostToDevice);
@@ -357,8 +357,13 @@ bool Executor::try_ladder(const Op& op) {
       e.rows_p = ((int64_t)np + 255) / 256 * 256;
       e.ld = Kp;
       size_t bytes = (size_t)S * e.rows_p * Kp * sizeof(__nv_bfloat16);
-      if (cudaMalloc(&e.plus, bytes) != cudaSuccess || cudaMalloc(&e.minus, bytes) != cudaSuccess)
-        throw std::runtime_error("ladder W+- allocation failed: out of memory");
+      e.plus = dev_alloc(bytes, st_, false);
+      try {
+        e.minus = dev_alloc(bytes, st_, false);
+      } catch (...) {
+        dev_free(e.plus, st_, false);
+        throw;
+      }
       cudaMemsetAsync(e.plus, 0, bytes, st_);
       cudaMemsetAsync(e.minus, 0, bytes, st_);
       count_launches(1);
@@ -370,8 +375,13 @@ bool Executor::try_ladder(const Op& op) {
       e.rows_p = np;
       e.ld = np;
       size_t bytes = (size_t)np * np * sizeof(double);
-      if (cudaMalloc(&e.plus, bytes) != cudaSuccess || cudaMalloc(&e.minus, bytes) != cudaSuccess)
-        throw std::runtime_error("ladder W+- allocation failed: out of memory");
+      e.plus = dev_alloc(bytes, st_, false);
+      try {
+        e.minus = dev_alloc(bytes, st_, false);
+      } catch (...) {
+        dev_free(e.plus, st_, false);
+        throw;
+      }
       count_launches(1);
       k_pack_w_pm<false><<<grid_of((int64_t)np * np), 256, 0, st_>>>(Wp, v_, pairs, np, 0, np, 0, nullptr, nullptr,
                                                                    (double*)e.plus, (double*)e.minus);
@@ -399,9 +409,14 @@ bool Executor::try_ladder(const Op& op) {
   if (mixed) {
     const int64_t rows_p = (nrows + 127) / 128 * 128;
     size_t bytes = (size_t)S * rows_p * Kp * sizeof(__nv_bfloat16);
-    void *ap = nullptr, *am = nullptr;
-    if (cudaMallocAsync(&ap, bytes, st_) != cudaSuccess || cudaMallocAsync(&am, bytes, st_) != cudaSuccess)
-      throw std::runtime_error("ladder operand allocation failed: out of memory");
+    void* ap = dev_alloc(bytes, st_, true);
+    void* am = nullptr;
+    try {
+      am = dev_alloc(bytes, st_, true);
+    } catch (...) {
+      dev_free(ap, st_, true);
+      throw;
+    }
     cudaMemsetAsync(ap, 0, bytes, st_);
     cudaMemsetAsync(am, 0, bytes, st_);
     if (sym) {
@@ -427,8 +442,8 @@ bool Executor::try_ladder(const Op& op) {
            1.0, 0.0);
     prof_end(r2, true);
     nvtxRangePop();
-    cudaFreeAsync(ap, st_);
-    cudaFreeAsync(am, st_);
+    dev_free(ap, st_, true);
+    dev_free(am, st_, true);
     stats.tc_calls += 2;
     stats.tc_flops += 2 * flops_each;
   } else {

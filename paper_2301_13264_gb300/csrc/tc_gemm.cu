@@ -31,6 +31,7 @@
 #include <string>
 #include <utility>
 
+#include "alloc.h"
 #include "exec.h"
 #include "fp64_tc.h"
 #include "tcgen05.cuh"
@@ -67,6 +68,10 @@ struct Params {
   // off(x; g) decomposes x row-major over g.ext and sums the coordinates times g.s0
   int ostr;
   Strided om, on;
+  int mt, nt, group_m;  // output tiles (rows, columns) and rows per raster group (raster_tile)
+  long long budget;  // clock cycles a producer or MMA wait may take before the kernel gives up
+  int stall;         // failure injection for tests: the producer issues no loads, so the MMA
+                     // issuer's first wait runs out after `budget` and the kernel reports it
 };
 
 __device__ __forceinline__ long long dim_offset(long long x, const Strided& g) {
@@ -93,7 +98,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  int tm, tn;
+  raster_tile(blockIdx.x, p.mt, p.nt, p.group_m, tm, tn);
+  const int m0 = tm * BM, n0 = tn * BN;
   const int total = p.nprod * p.kt_per_prod;
   const int it0 = blockIdx.z * p.it_per_split;
   const int it1 = min(total, it0 + p.it_per_split);
@@ -124,10 +131,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       int issued = 0;
       bool ok = true;
-      for (int it = 0; it < iters; ++it) {
+      for (int it = 0; it < (p.stall ? 0 : iters); ++it) {
         const int s = it % STAGES;
         const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, err)) {
+        if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, err, p.budget)) {
           ok = false;
           break;
         }
@@ -157,7 +164,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int it = 0; it < iters; ++it) {
         const int s = it % STAGES;
         const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(full0 + 8 * s, ph, err)) {
+        if (!mbar_wait(full0 + 8 * s, ph, err, p.budget)) {
           ok = false;
           break;
         }
@@ -316,7 +323,7 @@ void Executor::drop_cache_range(const double* p, int64_t n) {
     CacheEntry* e = cache_[i];
     if (e->src >= p && e->src < p + n) {
       cudaStreamSynchronize(st_);  // no kernel may still read the slices
-      cudaFree(e->dev);
+      dev_free(e->dev, st_, false);
       cache_bytes_ -= e->bytes;
       delete e;
       cache_.erase(cache_.begin() + i);
@@ -335,25 +342,25 @@ void Executor::invalidate_frozen() {
 
 void Executor::clear_cache() {
   for (CacheEntry* e : cache_) {
-    if (e->dev) cudaFree(e->dev);
+    dev_free(e->dev, st_, false);
     delete e;
   }
   cache_.clear();
   ++cache_epoch_;
   for (WPM& w : wpm_) {
-    if (w.plus) cudaFree(w.plus);
-    if (w.minus) cudaFree(w.minus);
+    dev_free(w.plus, st_, false);
+    dev_free(w.minus, st_, false);
   }
   wpm_.clear();
   if (pairs_) {
-    cudaFree(pairs_);
+    dev_free(pairs_, st_, false);
     pairs_ = nullptr;
   }
-  for (LadderTables& t : ladder_tables_) cudaFree(t.dev);
+  for (LadderTables& t : ladder_tables_) dev_free(t.dev, st_, false);
   ladder_tables_.clear();
   cache_bytes_ = 0;
   if (tc_err_) {
-    cudaFree(tc_err_);
+    dev_free(tc_err_, st_, false);
     tc_err_ = nullptr;
   }
 }
@@ -363,6 +370,8 @@ int Executor::tc_error() {
   int h = 0;
   if (cudaMemcpyAsync(&h, tc_err_, sizeof(int), cudaMemcpyDeviceToHost, st_) != cudaSuccess) return -1;
   if (cudaStreamSynchronize(st_) != cudaSuccess) return -1;
+  // a raised flag is reported once: lower it so that the next call's kernels run again
+  if (h != 0 && cudaMemsetAsync(tc_err_, 0, sizeof(int), st_) != cudaSuccess) return -1;
   return h;
 }
 
@@ -371,8 +380,7 @@ int Executor::tc_error() {
 static __nv_bfloat16* make_slices(cudaStream_t st, const double* src, const Strided& g, int64_t rows, int64_t rows_p,
                                   int64_t K, int S, int64_t Kp) {
   size_t bytes = (size_t)S * rows_p * Kp * sizeof(__nv_bfloat16);
-  void* p = nullptr;
-  if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) throw std::runtime_error("tc operand allocation failed");
+  void* p = dev_alloc(bytes, st, true);
   if (Kp != K || rows_p != rows) cudaMemsetAsync(p, 0, bytes, st);
   const int64_t total = rows * K;
   const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
@@ -421,7 +429,7 @@ bool Executor::tc_contract(int M, int N, int K, const double* A, const Strided& 
   const int64_t Np = ((int64_t)N + BN - 1) / BN * BN;
   if (Np / BN > 65535) return false;
   if (!tc_err_) {
-    if (cudaMalloc(&tc_err_, sizeof(int)) != cudaSuccess) throw std::runtime_error("tc flag allocation failed");
+    tc_err_ = (int*)dev_alloc(sizeof(int), st_, false);
     cudaMemsetAsync(tc_err_, 0, sizeof(int), st_);
   }
   auto get = [&](const double* src, const Strided& g, int64_t rows, int64_t rows_p, bool cst, bool& owned) {
@@ -435,6 +443,7 @@ bool Executor::tc_contract(int M, int N, int K, const double* A, const Strided& 
     __nv_bfloat16* p = make_slices(st_, src, g, rows, rows_p, K, S, Kp);
     owned = !cst;
     if (cst) {
+      dev_keep(p);  // a cache entry: lives until the cache drops it
       CacheEntry* e = new CacheEntry{src, g, rows_p, (int64_t)K, S, p, (size_t)S * rows_p * Kp * 2};
       cache_.push_back(e);
       cache_bytes_ += e->bytes;
@@ -445,8 +454,8 @@ bool Executor::tc_contract(int M, int N, int K, const double* A, const Strided& 
   __nv_bfloat16* a = get(A, ag, M, Mp, a_const, ownA);
   __nv_bfloat16* b = get(B, bg, N, Np, b_const, ownB);
   tc_run(a, Mp, b, Np, K, Kp, S, M, N, C, sCm, sCn, alpha, beta, om, on, BN, ch.nsplit);
-  if (ownA) cudaFreeAsync(a, st_);
-  if (ownB) cudaFreeAsync(b, st_);
+  if (ownA) dev_free(a, st_, true);
+  if (ownB) dev_free(b, st_, true);
   return true;
 }
 
@@ -469,7 +478,7 @@ bool Executor::fp64tc_contract(int M, int N, int K, const double* A, const Strid
   const int64_t Np = ((int64_t)N + oz::BN - 1) / oz::BN * oz::BN;
   if (Np / oz::BN > 65535) return false;
   if (!tc_err_) {
-    if (cudaMalloc(&tc_err_, sizeof(int)) != cudaSuccess) throw std::runtime_error("tc flag allocation failed");
+    tc_err_ = (int*)dev_alloc(sizeof(int), st_, false);
     cudaMemsetAsync(tc_err_, 0, sizeof(int), st_);
   }
   auto get = [&](const double* src, const Strided& g, int64_t rows, int64_t rows_p, bool cst, bool& owned) {
@@ -481,11 +490,11 @@ bool Executor::fp64tc_contract(int M, int N, int K, const double* A, const Strid
         }
     }
     const size_t bytes = oz::operand_bytes(rows_p, Kp);
-    void* p = nullptr;
-    if (cudaMallocAsync(&p, bytes, st_) != cudaSuccess) throw std::runtime_error("tc operand allocation failed");
+    void* p = dev_alloc(bytes, st_, true);
     oz::pack(st_, src, g, rows, rows_p, K, Kp, p);
     owned = !cst;
     if (cst) {
+      dev_keep(p);  // a cache entry: lives until the cache drops it
       CacheEntry* e = new CacheEntry{src, g, rows_p, (int64_t)K, oz::S, p, bytes};
       cache_.push_back(e);
       cache_bytes_ += e->bytes;
@@ -495,9 +504,10 @@ bool Executor::fp64tc_contract(int M, int N, int K, const double* A, const Strid
   bool ownA = false, ownB = false;
   void* a = get(A, ag, M, Mp, a_const, ownA);
   void* b = get(B, bg, N, Np, b_const, ownB);
-  last_tc_issued = oz::gemm(st_, a, Mp, b, Np, Kp, M, N, C, sCm, sCn, alpha, beta, om, on, 0, tc_err_);
-  if (ownA) cudaFreeAsync(a, st_);
-  if (ownB) cudaFreeAsync(b, st_);
+  last_tc_issued = oz::gemm(st_, a, Mp, b, Np, Kp, M, N, C, sCm, sCn, alpha, beta, om, on, 0, tc_err_,
+                            wait_cycles > 0 ? wait_cycles : tc::TIMEOUT_CYCLES);
+  if (ownA) dev_free(a, st_, true);
+  if (ownB) dev_free(b, st_, true);
   return true;
 }
 
@@ -523,11 +533,13 @@ Executor::TcChoice Executor::tc_choice(int M, int N, int64_t Kp, int S, bool str
   void *a = nullptr, *b = nullptr;
   double* C = nullptr;
   const size_t abytes = (size_t)S * Mp * Kp * 2, bbytes = (size_t)S * Nmax * Kp * 2;
-  if (cudaMalloc(&a, abytes) != cudaSuccess || cudaMalloc(&b, bbytes) != cudaSuccess ||
-      cudaMalloc((void**)&C, (size_t)M * N * sizeof(double)) != cudaSuccess) {
-    cudaFree(a);
-    cudaFree(b);
-    cudaGetLastError();
+  try {
+    a = dev_alloc(abytes, st_, false);
+    b = dev_alloc(bbytes, st_, false);
+    C = (double*)dev_alloc((size_t)M * N * sizeof(double), st_, false);
+  } catch (const OutOfMemory&) {
+    dev_free(a, st_, false);
+    dev_free(b, st_, false);
     return ch;  // no room to tune: keep the heuristic
   }
   cudaMemsetAsync(a, 0, abytes, st_);
@@ -566,9 +578,9 @@ Executor::TcChoice Executor::tc_choice(int M, int N, int64_t Kp, int S, bool str
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamSynchronize(st_);
-  cudaFree(a);
-  cudaFree(b);
-  cudaFree(C);
+  dev_free(a, st_, false);
+  dev_free(b, st_, false);
+  dev_free(C, st_, false);
   tc_tuned_[key] = ch;
   return ch;
 }
@@ -580,7 +592,7 @@ void Executor::tc_run(const void* a, int64_t Mp, const void* b, int64_t Np, int 
   if (BN == 0) BN = tile_width(N);
   if (Np % BN != 0 || Mp % tc::BM != 0 || Np / BN > 65535) throw std::runtime_error("tc_run: bad padding");
   if (!tc_err_) {
-    if (cudaMalloc(&tc_err_, sizeof(int)) != cudaSuccess) throw std::runtime_error("tc flag allocation failed");
+    tc_err_ = (int*)dev_alloc(sizeof(int), st_, false);
     cudaMemsetAsync(tc_err_, 0, sizeof(int), st_);
   }
   CUtensorMap ta = tc::make_map(a, Mp, Kp, S, tc::BM);
@@ -616,11 +628,15 @@ void Executor::tc_run(const void* a, int64_t Mp, const void* b, int64_t Np, int 
   } else {
     p.om.ndim = p.on.ndim = 0;
   }
-  if (nsplit > 1) {
-    if (cudaMallocAsync((void**)&p.part, (size_t)nsplit * M * N * sizeof(double), st_) != cudaSuccess)
-      throw std::runtime_error("tc split workspace allocation failed");
-  }
-  dim3 grid((unsigned)(Mp / tc::BM), (unsigned)(Np / BN), (unsigned)nsplit);
+  p.budget = wait_cycles > 0 ? wait_cycles : tc::TIMEOUT_CYCLES;
+  p.stall = stall_next ? 1 : 0;
+  stall_next = false;
+  if (nsplit > 1) p.part = (double*)dev_alloc((size_t)nsplit * M * N * sizeof(double), st_, true);
+  if ((Mp / tc::BM) * (Np / BN) > (int64_t)INT32_MAX) throw std::runtime_error("tc_run: too many tiles");
+  p.mt = (int)(Mp / tc::BM);
+  p.nt = (int)(Np / BN);
+  p.group_m = tc::raster_group(p.mt, BN);
+  dim3 grid((unsigned)(p.mt * p.nt), 1u, (unsigned)nsplit);
   last_tc_issued = 2.0 * (double)Mp * (double)Np * (double)Kp * p.nprod;
   if (BN == 256)
     launch_tc<256>(grid, ta, tb, p, st_);
@@ -633,7 +649,7 @@ void Executor::tc_run(const void* a, int64_t Mp, const void* b, int64_t Np, int 
     count_launches(1);
     tc::k_tc_reduce<<<(int)std::min<long long>((tot + 255) / 256, 152 * 16), 256, 0, st_>>>(
         M, N, nsplit, p.part, C, sCm, sCn, p.beta_zero, p.ostr, p.om, p.on);
-    cudaFreeAsync(p.part, st_);
+    dev_free(p.part, st_, true);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw std::runtime_error(std::string("tc gemm launch: ") + cudaGetErrorString(e));

@@ -1,6 +1,7 @@
 // tcgen05 / TMA / mbarrier building blocks shared by the tensor-core kernels
-// (inline PTX for sm_103a).  Every wait is bounded: mbar_wait gives up after
-// TIMEOUT_CYCLES or when another CTA has raised the error flag.
+// (inline PTX for sm_103a).  Every wait is bounded: mbar_wait gives up after its
+// budget (TIMEOUT_CYCLES unless the launch passes a shorter one) or when another
+// CTA has raised the error flag.
 #pragma once
 
 #include <cuda.h>
@@ -36,15 +37,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait for the phase of the given parity; false on timeout or when
-// another CTA has raised the error flag.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* err) {
+// Bounded wait for the phase of the given parity; false after `budget` clock cycles
+// or when another CTA has raised the error flag.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* err,
+                                          long long budget = TIMEOUT_CYCLES) {
   long long t0 = clock64();
   for (uint32_t i = 0;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 255u) == 255u) {
       if (*err) return false;
-      if (clock64() - t0 > TIMEOUT_CYCLES) return false;
+      if (clock64() - t0 > budget) return false;
     }
   }
 }
@@ -104,6 +106,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Grouped rasterisation of a 1-D grid over the mt x nt output tiles of a GEMM: consecutive
+// CTAs take group_m row tiles of one column tile before moving on to the next column tile,
+// so that the CTAs resident at the same time cover about group_m x (152 / group_m) tiles and
+// share both operands' K strips through L2.  (Row tile fastest over the whole grid would
+// give every resident CTA a private A strip: for the o^3 v^3 ring contractions that alone
+// asks ~4 TB/s of DRAM at the tensor rate.)
+__device__ __forceinline__ void raster_tile(int L, int mt, int nt, int group_m, int& tm, int& tn) {
+  const int per_group = group_m * nt;
+  const int g = L / per_group;
+  const int first = g * group_m;
+  const int gm = min(mt - first, group_m);
+  const int r = L - g * per_group;
+  tm = first + r % gm;
+  tn = r / gm;
+}
+
+// Rows of tiles per raster group for a tile of 128 x bn: resident tiles about square in
+// the bytes they read (group_m * 128 ~ (152 / group_m) * bn), at most mt.
+inline int raster_group(int mt, int bn) {
+  const int g = bn >= 256 ? 16 : (bn >= 128 ? 12 : 8);
+  return mt < g ? mt : g;
 }
 
 // 3-D TMA map over bf16 slices [S][rows][Kp]: boxes of 64 K x box_rows rows x 1 slice,
