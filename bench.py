@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--mlp", action="store_true", help="instead, time the learned-guess kernels at the workload size")
     ap.add_argument("--batch-eom", type=int, default=0,
                     help="with --batch: time the batched right EOM solve for this many roots instead")
+    ap.add_argument("--guess-eval", action="store_true",
+                    help="instead, train the learned starts on smaller systems and compare iterations at the workload")
+    ap.add_argument("--guess-train", type=int, default=40, help="--guess-eval: number of training systems")
+    ap.add_argument("--guess-scale", type=float, default=4.0, help="--guess-eval: size reduction of the training systems")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -654,8 +658,71 @@ def run_mlp(args):
                       "peak_source": f"bf16_tflops of {src} MEASURED_PEAKS.json"}), flush=True)
 
 
+def run_guess_eval(args):
+    """The learned starts at the workload's size: train the doubles network (t_CCSD - t_MP2)
+    and the multiplier network (lambda - (-eta/D)) on solved systems of the same generator
+    at a reduced size (o, v and naux divided by args.guess_scale, seeds 1000...), then solve
+    the workload's ground state and Lambda equations to residual 1e-7 from the plain and the
+    learned starts, and report iteration counts and the distance of each start from the
+    converged doubles."""
+    import torch
+    from paper_2301_13264_gb300 import binding as B
+    from paper_2301_13264_gb300 import learned_guess as lg
+    from paper_2301_13264_gb300.synth import WORKLOADS, make_hamiltonian, workload
+
+    wl = WORKLOADS[args.workload]
+    f = args.guess_scale
+    to, tv, tx = max(2, round(wl["o"] / f)), max(4, round(wl["v"] / f)), max(8, round(wl["naux"] / f))
+    systems = [make_hamiltonian(to, tv, tx, seed=1000 + s) for s in range(args.guess_train)]
+    t0 = time.perf_counter()
+    topt = B.ccsd_default_options(tol_res=1e-8, tol_lin=1e-8)
+    models, losses = {}, {}
+    for name, which in (("amplitudes", B.GUESS_AMPLITUDES), ("multipliers", B.GUESS_MULTIPLIERS)):
+        X, T = lg.generate(systems, topt, rows_per_system=min(20000, to * to * tv * tv), seed=3, which=which)
+        models[name], losses[name] = lg.train(X, T, steps=3000, batch=8192, lr=2e-3, seed=5)
+    train_s = time.perf_counter() - t0
+    H = workload(args.workload)
+    o, v = H.o, H.v
+    opt = B.ccsd_default_options(precision=B.PREC_MIXED, splits=args.splits, tol_res=1e-7, tol_lin=1e-7,
+                                 max_iter=300)
+    out = {}
+    for name in ("plain", "learned"):
+        h = B.ccsd_create(H.eps, H.h, H.B, o, v, H.naux, opt)
+        try:
+            if name == "learned":
+                B.ccsd_set_guess_model(h, models["amplitudes"])
+                B.ccsd_set_multiplier_guess_model(h, models["multipliers"])
+            mt = models["amplitudes"] if name == "learned" else None
+            mm = models["multipliers"] if name == "learned" else None
+            st = lg.guess_doubles(h, o, v, mt).ravel()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            e, _ = B.ccsd_solve_ground(h)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t1
+            it = B.ccsd_solve_iterations(h)
+            sm = lg.guess_doubles(h, o, v, mm, which=B.GUESS_MULTIPLIERS).ravel()
+            dim = B.vector_dim(o, v)
+            t, lam = np.zeros(dim), np.zeros(dim)
+            B.ccsd_get_amplitudes(h, t, lam)
+            out[name] = {"ground_iterations": it["ground"], "lambda_iterations": it["lambda"],
+                         "ground_and_lambda_s": secs, "e_ccsd": e,
+                         "start_error_doubles": float(np.linalg.norm(st - t[o * v:])),
+                         "start_error_multipliers": float(np.linalg.norm(sm - lam[o * v:]))}
+        finally:
+            B.ccsd_destroy(h)
+    print(json.dumps({"metric": "iterations to residual 1e-7 from the learned and the plain starts",
+                      "workload": f"{args.workload} o={o} v={v} naux={H.naux}",
+                      "training": {"systems": len(systems), "o": to, "v": tv, "naux": tx, "seconds": train_s,
+                                   "final_loss": losses},
+                      "precision": f"mixed S={args.splits}, refined", "results": out}), flush=True)
+
+
 def main():
     args = parse()
+    if args.guess_eval:
+        run_guess_eval(args)
+        return
     if args.mlp:
         run_mlp(args)
         return

@@ -191,6 +191,20 @@ ccsd_status ccsd_gradient_densities(ccsd_handle h, int k, double* D, double* Z);
  * sum_pq D_pq dh_pq + sum_Jpq Z_Jpq dB_Jpq with the densities of ccsd_gradient_densities. */
 ccsd_status ccsd_energy_gradient(ccsd_handle h, int k, int ndir, const double* dh, const double* dB, double* g);
 
+/* One-electron transition density D[n*n], D_pq = <psi_k^L| E_pq |psi_l^R> at the solved
+ * states (k != l; k, l = 0 the ground state), the density the orbital-connection term and
+ * the orbital multipliers are built from (section on orbital connections; Implementation,
+ * k-eta^1).  Host or device memory. */
+ccsd_status ccsd_transition_density(ccsd_handle h, int k, int l, double* D);
+
+/* Orbital-connection term of the coupling (section "Significance of orbital connections"):
+ * O[d] = sum_rs (D_rs - D_sr)/2 W[d]_rs with D the (k, l) transition density and W[d][n*n]
+ * the ket derivative <phi_r|d phi_s/dx_d> of the unmodified orbitals along each of ndir
+ * directions (host or device).  With the symmetric connection T = S^(-1/2) the coupling is
+ * ccsd_derivative_coupling along the symmetric-connection Hamiltonian derivative plus O; with
+ * the natural connection (the library's default reading) the term is absent. */
+ccsd_status ccsd_connection_term(ccsd_handle h, int k, int l, int ndir, const double* W, double* O);
+
 /* Branching plane of the excited states k and l (1 <= k, l, k != l) over ndir coordinate
  * directions taken as orthonormal (Results section, the conical-intersection search):
  *   out[0..ndir)        g = grad (E_l - E_k)
@@ -249,6 +263,27 @@ ccsd_status ccsd_guess_features(ccsd_handle h, float* X);
 /* Use `model` for the starting doubles of the next ccsd_solve_ground (NULL: the
  * MP2-type start).  The model is copied. */
 ccsd_status ccsd_set_guess_model(ccsd_handle h, const float* model);
+
+/* The same network for the multiplier equations x^T A = -rhs^T (Lambda, lambda^T A = -eta^T,
+ * and the zeta equations of Eq. amplituderelax and of the state-energy gradients): their
+ * start is the Jacobi step x = -rhs/D, whose doubles take the place of t_MP2 in the
+ * features (x_2, D, |(ia|jb)|) and are corrected by the model's prediction.  A model for
+ * this is trained on converged ground multipliers (CCSD_GUESS_MULTIPLIERS below).  NULL:
+ * the Jacobi start.  The converged multipliers do not depend on the start. */
+ccsd_status ccsd_set_multiplier_guess_model(ccsd_handle h, const float* model);
+
+enum { CCSD_GUESS_AMPLITUDES = 0, CCSD_GUESS_MULTIPLIERS = 1 };
+/* Training rows from the handle's solved ground state: X[o*o*v*v][3] the features of the
+ * start and T[o*o*v*v] = converged doubles - start doubles.  which = CCSD_GUESS_AMPLITUDES:
+ * start t_MP2, converged t2; CCSD_GUESS_MULTIPLIERS: start -eta/D, converged lambda.
+ * Host or device memory; CCSD_ERR_STATE before ccsd_solve_ground. */
+ccsd_status ccsd_guess_targets(ccsd_handle h, int which, float* X, float* T);
+/* x2[o*o*v*v] (FP64) = the starting doubles a solve would use with `model` (NULL: the plain
+ * start t_MP2, or -eta/D for CCSD_GUESS_MULTIPLIERS, which needs the ground state). */
+ccsd_status ccsd_guess_doubles(ccsd_handle h, int which, const float* model, double* x2);
+/* Iterations of the handle's last ground-state solve, Lambda solve and zeta solve (any
+ * pointer may be NULL); with refinement they count the mixed and FP64 iterations together. */
+ccsd_status ccsd_solve_iterations(ccsd_handle h, int* ground, int* lambda, int* zeta);
 
 /* ---- batches of systems -----------------------------------------------------
  * Many small systems underuse the GPU one at a time.  A batch groups handles

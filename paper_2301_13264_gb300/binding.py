@@ -245,6 +245,16 @@ def ccsd_branching_plane(h, k, l, ndir, dh, dB):
     return v[:ndir], v[ndir:2 * ndir], v[2 * ndir:]
 
 
+def ccsd_transition_density(h, k, l, D):
+    _check(h, lib().ccsd_transition_density(h, k, l, _ptr(D)))
+
+
+def ccsd_connection_term(h, k, l, ndir, W):
+    O = (ctypes.c_double * ndir)()
+    _check(h, lib().ccsd_connection_term(h, k, l, ndir, _ptr(W), O))
+    return list(O)
+
+
 def ccsd_derivative_coupling_noalloc(h, k, l, ndir, dh, dB):
     """Allocation-free variant; dh and dB must be device tensors, densities held."""
     F = (ctypes.c_double * ndir)()
@@ -392,6 +402,33 @@ def ccsd_guess_features(h, X):
 def ccsd_set_guess_model(h, model):
     f = _mlp_fn("ccsd_set_guess_model", [_P, _P])
     _check(h, f(h, None if model is None else _fptr(model, MLP_PARAMS)))
+
+
+GUESS_AMPLITUDES, GUESS_MULTIPLIERS = 0, 1
+
+
+def ccsd_set_multiplier_guess_model(h, model):
+    """Learned start for the multiplier solves (None: the Jacobi start)."""
+    f = _mlp_fn("ccsd_set_multiplier_guess_model", [_P, _P])
+    _check(h, f(h, None if model is None else _fptr(model, MLP_PARAMS)))
+
+
+def ccsd_guess_targets(h, which, X, T):
+    """Fill X[n2][3] (float32) with a start's features and T[n2] with converged - start doubles."""
+    f = _mlp_fn("ccsd_guess_targets", [_P, ctypes.c_int, _P, _P])
+    _check(h, f(h, which, _fptr(X), _fptr(T)))
+
+
+def ccsd_guess_doubles(h, which, model, x2):
+    """x2[n2] (float64) = the start's doubles, corrected by `model` when given."""
+    f = _mlp_fn("ccsd_guess_doubles", [_P, ctypes.c_int, _P, _P])
+    _check(h, f(h, which, None if model is None else _fptr(model, MLP_PARAMS), _ptr(x2)))
+
+
+def ccsd_solve_iterations(h):
+    g, l, z = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(h, lib().ccsd_solve_iterations(h, ctypes.byref(g), ctypes.byref(l), ctypes.byref(z)))
+    return {"ground": g.value, "lambda": l.value, "zeta": z.value}
 
 
 # ---- batches of systems -----------------------------------------------------

@@ -104,6 +104,8 @@ struct ccsd_ctx {
   DevBuf Dd, Zd;
   long long prof_launch0 = 0;
   DevBuf guess_model;  // MLP model (floats) for the starting doubles, or empty
+  DevBuf mult_model;   // MLP model for the starting doubles of the multiplier solves, or empty
+  int iters_ground = 0, iters_lambda = 0, iters_zeta = 0;  // of the last solves
   // orbital relaxation (relax_orbitals): Hartree-Fock programs on the handle's (h, B)
   std::unique_ptr<HFPrograms> hfp;
   std::unique_ptr<Executor> hx;
@@ -1187,6 +1189,22 @@ void add_orbital_relaxation(ccsd_ctx* c, int k, int l, bool overlap = true) {
   sync(c);
 }
 
+// Start of a multiplier solve x^T A = -rhs^T: the Jacobi step x = -rhs/D, its doubles
+// corrected, when the handle has a multiplier model, by the model's prediction from the
+// per-element features (x_2, D, |(ia|jb)|).
+void multiplier_start(ccsd_ctx* c, const double* rhs, double* x) {
+  launch_precond(c->vs, c->eps.p, rhs, x, 0.0, c->st);
+  launch_axpby(c->dim, 0.0, x, -1.0, x, c->st);
+  if (!c->mult_model.p) return;
+  const int64_t n2 = c->dim - c->n1;
+  DevBuf X((n2 * 3 + 1) / 2), delta((n2 + 1) / 2);
+  const double* gov = c->ex->ptr(c->P.cp.g.id("Govov"));
+  mlp::features(gov, c->eps.p, c->o, c->v, (float*)X.p, c->st, x + c->n1);
+  mlp::predict((const float*)c->mult_model.p, (const float*)X.p, n2, (float*)delta.p, c->st);
+  mlp::add_delta(x + c->n1, (const float*)delta.p, n2, c->st);
+  sync(c);
+}
+
 void compute_densities(ccsd_ctx* c, int k, int l) {
   const int nr = (int)c->omega.size();
   if (k < 0 || l < 0 || k == l) throw Err(CCSD_ERR_ARG, "state indices must differ and be >= 0");
@@ -1231,9 +1249,8 @@ void compute_densities(ccsd_ctx* c, int k, int l) {
     }
     launch_axpby(dim, 1.0, hv.p, 1.0, teta.p, c->st);
     // zeta^T A = -t-eta^T (Eq. amplituderelax)
-    launch_precond(c->vs, c->eps.p, teta.p, zeta.p, 0.0, c->st);
-    launch_axpby(dim, 0.0, zeta.p, -1.0, zeta.p, c->st);
-    solve_left_refined(c, teta.p, zeta.p, c->opt.tol_lin);
+    multiplier_start(c, teta.p, zeta.p);
+    c->iters_zeta = solve_left_refined(c, teta.p, zeta.p, c->opt.tol_lin);
     launch_weight(c->vs, zeta.p, Wz.p, 1, dim, c->st);
     launch_weight(c->vs, gam.p, Wg.p, 1, dim, c->st);
     CUDA_OK(cudaMemcpyAsync(s0.p, &g0, sizeof(double), cudaMemcpyHostToDevice, c->st));
@@ -1306,9 +1323,8 @@ void compute_gradient_densities(ccsd_ctx* c, int k) {
       hess_right(c, 0.0, Lk, Rk, hv.p);
     }
     // zeta^T A = -(F(L_k) R_k)^T
-    launch_precond(c->vs, c->eps.p, hv.p, zeta.p, 0.0, c->st);
-    launch_axpby(dim, 0.0, zeta.p, -1.0, zeta.p, c->st);
-    solve_left_refined(c, hv.p, zeta.p, c->opt.tol_lin);
+    multiplier_start(c, hv.p, zeta.p);
+    c->iters_zeta = solve_left_refined(c, hv.p, zeta.p, c->opt.tol_lin);
     launch_weight(c->vs, zeta.p, Wz.p, 1, dim, c->st);
     launch_weight(c->vs, Lk, WL.p, 1, dim, c->st);
     CUDA_OK(cudaMemsetAsync(s0.p, 0, sizeof(double), c->st));
@@ -1623,9 +1639,9 @@ ccsd_status ccsd_solve_ground(ccsd_handle c, double* e_ccsd, int* iters) {
       PrecScope p(c, refine ? fp64_prec(c) : c->ex->precision());
       left_block(c, zero.p, c->eta.p, 1, 1.0);
     }
-    launch_precond(c->vs, c->eps.p, c->eta.p, c->lam.p, 0.0, c->st);
-    launch_axpby(dim, 0.0, c->lam.p, -1.0, c->lam.p, c->st);
-    solve_left_refined(c, c->eta.p, c->lam.p, c->opt.tol_lin);
+    multiplier_start(c, c->eta.p, c->lam.p);
+    c->iters_lambda = solve_left_refined(c, c->eta.p, c->lam.p, c->opt.tol_lin);
+    c->iters_ground = it;
     if (e_ccsd) *e_ccsd = e;
     if (iters) *iters = it;
   });
@@ -1706,9 +1722,8 @@ ccsd_status ccsd_set_amplitudes(ccsd_handle c, const double* t, const double* la
     if (lambda) {
       CUDA_OK(cudaMemcpyAsync(c->lam.p, lambda, dim * sizeof(double), cudaMemcpyDefault, c->st));
     } else {
-      launch_precond(c->vs, c->eps.p, c->eta.p, c->lam.p, 0.0, c->st);
-      launch_axpby(dim, 0.0, c->lam.p, -1.0, c->lam.p, c->st);
-      solve_left_refined(c, c->eta.p, c->lam.p, c->opt.tol_lin);
+      multiplier_start(c, c->eta.p, c->lam.p);
+      c->iters_lambda = solve_left_refined(c, c->eta.p, c->lam.p, c->opt.tol_lin);
     }
     sync(c);
     if (e) *e = en;
@@ -1753,6 +1768,60 @@ ccsd_status ccsd_derivative_coupling(ccsd_handle c, int k, int l, int ndir, cons
     if (ndir < 1 || !dh || !dB || !F) throw Err(CCSD_ERR_ARG, "bad arguments");
     compute_densities(c, k, l);
     contract_densities(c, ndir, dh, dB, F);
+  });
+}
+
+// checks of the state indices of a transition density (k, l) and the states it needs
+void check_pair(ccsd_ctx* c, int k, int l) {
+  const int nr = (int)c->omega.size();
+  if (k < 0 || l < 0 || k == l) throw Err(CCSD_ERR_ARG, "state indices must differ and be >= 0");
+  if (!c->have_ground) throw Err(CCSD_ERR_STATE, "ground state not solved");
+  if (k > nr || l > nr) throw Err(CCSD_ERR_ARG, "state index beyond the solved roots");
+  if ((k > 0 || l > 0) && !(c->have_right && c->have_left)) throw Err(CCSD_ERR_STATE, "EOM states not solved");
+}
+
+ccsd_status ccsd_transition_density(ccsd_handle c, int k, int l, double* D) {
+  return guarded(c, [&] {
+    if (!D) throw Err(CCSD_ERR_ARG, "null pointer");
+    check_pair(c, k, l);
+    ensure_cache(c);
+    const int64_t nn = (int64_t)c->n * c->n;
+    DevBuf Dt(nn);
+    {
+      PrecScope fp64(c, refining(c) ? fp64_prec(c) : c->ex->precision());
+      transition_density(c, k, l, Dt.p);
+    }
+    from_device(c, Dt.p, nn, D);
+    sync(c);
+  });
+}
+
+ccsd_status ccsd_connection_term(ccsd_handle c, int k, int l, int ndir, const double* W, double* O) {
+  return guarded(c, [&] {
+    if (ndir < 1 || !W || !O) throw Err(CCSD_ERR_ARG, "bad arguments");
+    check_pair(c, k, l);
+    ensure_cache(c);
+    const int n = c->n;
+    const int64_t nn = (int64_t)n * n;
+    DevBuf Dt(nn), Da(nn), out(1), tmp;
+    {
+      PrecScope fp64(c, refining(c) ? fp64_prec(c) : c->ex->precision());
+      transition_density(c, k, l, Dt.p);
+    }
+    // Da = (D - D^T) / 2, then O[d] = <Da, W[d]>
+    launch_antisymmetric_part(n, Dt.p, Da.p, c->st);
+    const bool wdev = is_device_ptr(W);
+    double* work = c->ex->scratch(1024);
+    for (int d = 0; d < ndir; ++d) {
+      const double* wp = W + d * nn;
+      if (!wdev) {
+        to_device(c, wp, nn, tmp);
+        wp = tmp.p;
+      }
+      launch_dot(nn, Da.p, wp, out.p, work, c->st);
+      CUDA_OK(cudaMemcpyAsync(O + d, out.p, sizeof(double), cudaMemcpyDefault, c->st));
+      sync(c);
+    }
   });
 }
 
@@ -1973,6 +2042,77 @@ ccsd_status ccsd_set_guess_model(ccsd_handle c, const float* model) {
       return;
     }
     floats_to_device(model, mlp::kParams, c->guess_model);
+  });
+}
+
+ccsd_status ccsd_set_multiplier_guess_model(ccsd_handle c, const float* model) {
+  return guarded(c, [&] {
+    if (!model) {
+      c->mult_model.release();
+      return;
+    }
+    floats_to_device(model, mlp::kParams, c->mult_model);
+  });
+}
+
+ccsd_status ccsd_guess_targets(ccsd_handle c, int which, float* X, float* T) {
+  return guarded(c, [&] {
+    if (!X || !T || (which != CCSD_GUESS_AMPLITUDES && which != CCSD_GUESS_MULTIPLIERS))
+      throw Err(CCSD_ERR_ARG, "bad arguments");
+    if (!c->have_ground) throw Err(CCSD_ERR_STATE, "ground state not solved");
+    const int64_t n2 = c->dim - c->n1;
+    const double* gov = c->ex->ptr(c->P.cp.g.id("Govov"));
+    DevBuf dX((n2 * 3 + 1) / 2), dT((n2 + 1) / 2), x0;
+    const double* start = nullptr;  // amplitudes: t_MP2 from the integrals
+    const double* conv = c->t.p + c->n1;
+    if (which == CCSD_GUESS_MULTIPLIERS) {
+      x0.alloc(c->dim);
+      launch_precond(c->vs, c->eps.p, c->eta.p, x0.p, 0.0, c->st);
+      launch_axpby(c->dim, 0.0, x0.p, -1.0, x0.p, c->st);
+      start = x0.p + c->n1;
+      conv = c->lam.p + c->n1;
+    }
+    mlp::features(gov, c->eps.p, c->o, c->v, (float*)dX.p, c->st, start);
+    mlp::targets(conv, (const float*)dX.p, n2, (float*)dT.p, c->st);
+    CUDA_OK(cudaMemcpyAsync(X, dX.p, n2 * 3 * sizeof(float), cudaMemcpyDefault, c->st));
+    CUDA_OK(cudaMemcpyAsync(T, dT.p, n2 * sizeof(float), cudaMemcpyDefault, c->st));
+    sync(c);
+  });
+}
+
+ccsd_status ccsd_guess_doubles(ccsd_handle c, int which, const float* model, double* x2) {
+  return guarded(c, [&] {
+    if (!x2 || (which != CCSD_GUESS_AMPLITUDES && which != CCSD_GUESS_MULTIPLIERS))
+      throw Err(CCSD_ERR_ARG, "bad arguments");
+    const int64_t n2 = c->dim - c->n1;
+    const double* gov = c->ex->ptr(c->P.cp.g.id("Govov"));
+    DevBuf start(c->dim), dX((n2 * 3 + 1) / 2);
+    if (which == CCSD_GUESS_MULTIPLIERS) {
+      if (!c->have_ground) throw Err(CCSD_ERR_STATE, "ground state not solved");
+      launch_precond(c->vs, c->eps.p, c->eta.p, start.p, 0.0, c->st);
+      launch_axpby(c->dim, 0.0, start.p, -1.0, start.p, c->st);
+      mlp::features(gov, c->eps.p, c->o, c->v, (float*)dX.p, c->st, start.p + c->n1);
+    } else {
+      // the first-order doubles t_MP2 = -(ia|jb)/D (FP64); the features carry them in FP32
+      mlp::features(gov, c->eps.p, c->o, c->v, (float*)dX.p, c->st);
+      mlp::mp2_doubles(gov, c->eps.p, c->o, c->v, start.p + c->n1, c->st);
+    }
+    if (model) {
+      DevBuf m, delta((n2 + 1) / 2);
+      floats_to_device(model, mlp::kParams, m);
+      mlp::predict((const float*)m.p, (const float*)dX.p, n2, (float*)delta.p, c->st);
+      mlp::add_delta(start.p + c->n1, (const float*)delta.p, n2, c->st);
+    }
+    from_device(c, start.p + c->n1, n2, x2);
+    sync(c);
+  });
+}
+
+ccsd_status ccsd_solve_iterations(ccsd_handle c, int* ground, int* lambda, int* zeta) {
+  return guarded(c, [&] {
+    if (ground) *ground = c->iters_ground;
+    if (lambda) *lambda = c->iters_lambda;
+    if (zeta) *zeta = c->iters_zeta;
   });
 }
 

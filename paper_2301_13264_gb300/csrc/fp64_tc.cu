@@ -366,23 +366,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
-// one warp per row: e_r with max_k |X_rk| < 2^e_r (0 for a zero row, NONFINITE for Inf/NaN)
-template <typename I>
-__global__ void k_oz_rowexp(const double* __restrict__ src, Strided g, I K, I rows, int* __restrict__ exps) {
+// offsets of a strided gather over dims [d0, d1): off[x] = sum_d coord_d(x) * g.s1[d]
+__global__ void k_oz_offsets(Strided g, int d0, int d1, int64_t n, int64_t* __restrict__ off) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = x, o = 0;
+    for (int d = d1 - 1; d >= d0; --d) {
+      const int64_t e = g.ext[d];
+      o += (r % e) * g.s1[d];
+      r /= e;
+    }
+    off[x] = o;
+  }
+}
+
+// one warp per row: e_r with max_k |X_rk| < 2^e_r (0 for a zero row, NONFINITE for Inf/NaN);
+// element (row, k) at src[rowoff[row] + koff[k]]
+__global__ void k_oz_rowexp(const double* __restrict__ src, const int64_t* __restrict__ rowoff,
+                            const int64_t* __restrict__ koff, int64_t K, int64_t rows, int* __restrict__ exps) {
   const int lane = threadIdx.x & 31;
-  const I wpb = blockDim.x >> 5;
-  for (I row = (I)blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += (I)gridDim.x * wpb) {
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t row = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += (int64_t)gridDim.x * wpb) {
+    const int64_t ro = rowoff[row];
     double m = 0.0;
     bool finite = true;
-    for (I k = lane; k < K; k += 32) {
-      I r = row * K + k;
-      int64_t off = 0;
-      for (int d = g.ndim - 1; d >= 0; --d) {
-        const I e = (I)g.ext[d];
-        off += (int64_t)(r % e) * g.s1[d];
-        r /= e;
-      }
-      const double x = fabs(src[off]);
+    for (int64_t k = lane; k < K; k += 32) {
+      const double x = fabs(src[ro + koff[k]]);
       if (!(x <= 1.7976931348623157e308)) finite = false;
       else m = fmax(m, x);
     }
@@ -397,28 +405,61 @@ __global__ void k_oz_rowexp(const double* __restrict__ src, Strided g, I K, I ro
   }
 }
 
-// the 7 slices of every element (rows < rows, k < K)
-template <typename I>
-__global__ void k_oz_pack(const double* __restrict__ src, Strided g, I K, I total, const int* __restrict__ exps,
-                          int64_t Kp, int64_t plane, __nv_bfloat16* __restrict__ dst) {
-  for (I idx = (I)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (I)gridDim.x * blockDim.x) {
-    I r = idx;
-    int64_t off = 0;
-    for (int d = g.ndim - 1; d >= 0; --d) {
-      const I e = (I)g.ext[d];
-      off += (int64_t)(r % e) * g.s1[d];
-      r /= e;
-    }
-    const I row = idx / K, k = idx % K;
-    const int e = exps[row];
-    __nv_bfloat16* dd = dst + (int64_t)row * Kp + k;
-    double y = (e == NONFINITE) ? 0.0 : ldexp(src[off], 6 - e);  // |y| < 64
+// the 7 slices of every element, padding rows and K zero: tiles of 32 rows x 64 k through
+// shared memory, read along k (along_rows = 0) or along the rows (along_rows = 1) as the
+// source is contiguous, written as bf16 pairs along k
+__global__ void __launch_bounds__(256) k_oz_pack(const double* __restrict__ src, const int64_t* __restrict__ rowoff,
+                                                 const int64_t* __restrict__ koff, int64_t rows, int64_t K,
+                                                 int64_t rows_p, int64_t Kp, int along_rows,
+                                                 const int* __restrict__ exps, __nv_bfloat16* __restrict__ dst) {
+  __shared__ double tile[32][65];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t ktiles = Kp / 64, ntiles = (rows_p / 32) * ktiles;
+  const int64_t plane = rows_p * Kp;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = (t / ktiles) * 32, k0 = (t % ktiles) * 64;
+    if (along_rows) {
+      const int64_t r = r0 + tx;
+      const int64_t ro = r < rows ? rowoff[r] : 0;
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      const double q = rint(y);                         // integer in [-64, 64]
-      dd[s * plane] = __double2bfloat16(ldexp(q, -7 * s));  // exact in bf16
-      y = (y - q) * 128.0;                              // exact; |y| <= 64
+      for (int i = 0; i < 8; ++i) {
+        const int kk = ty + 8 * i;
+        const int64_t k = k0 + kk;
+        tile[tx][kk] = (r < rows && k < K) ? src[ro + koff[k]] : 0.0;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int rr = ty + 8 * i;
+        const int64_t r = r0 + rr;
+        const int64_t ro = r < rows ? rowoff[r] : 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int kk = tx + 32 * h;
+          const int64_t k = k0 + kk;
+          tile[rr][kk] = (r < rows && k < K) ? src[ro + koff[k]] : 0.0;
+        }
+      }
     }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int rr = ty + 8 * i;
+      const int64_t r = r0 + rr;
+      const int e = r < rows ? exps[r] : NONFINITE;
+      double y0 = (e == NONFINITE) ? 0.0 : ldexp(tile[rr][2 * tx], 6 - e);  // |y| < 64
+      double y1 = (e == NONFINITE) ? 0.0 : ldexp(tile[rr][2 * tx + 1], 6 - e);
+      __nv_bfloat162* d = reinterpret_cast<__nv_bfloat162*>(dst + r * Kp + k0 + 2 * tx);
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const double q0 = rint(y0), q1 = rint(y1);  // integers in [-64, 64]
+        d[s * (plane / 2)] = __halves2bfloat162(__double2bfloat16(ldexp(q0, -7 * s)),  // exact in bf16
+                                                __double2bfloat16(ldexp(q1, -7 * s)));
+        y0 = (y0 - q0) * 128.0;  // exact; |y| <= 64
+        y1 = (y1 - q1) * 128.0;
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -426,23 +467,34 @@ size_t operand_bytes(int64_t rows_p, int64_t Kp) { return (size_t)S * rows_p * K
 
 void pack(cudaStream_t st, const double* src, const Strided& g, int64_t rows, int64_t rows_p, int64_t K, int64_t Kp,
           void* buf) {
-  if (rows < 1 || K < 1 || rows_p < rows || Kp < K) throw std::runtime_error("oz::pack: bad sizes");
+  if (rows < 1 || K < 1 || rows_p < rows || Kp < K || rows_p % 32 != 0 || Kp % 64 != 0)
+    throw std::runtime_error("oz::pack: bad sizes");
   int* exps = exps_of(buf, rows_p, Kp);
-  if (Kp != K || rows_p != rows) cudaMemsetAsync(buf, 0, (size_t)S * rows_p * Kp * 2, st);
   cudaMemsetAsync(exps, 0, (size_t)rows_p * 4, st);
-  const int64_t total = rows * K;
-  const int rgrid = (int)std::min<int64_t>((rows + 7) / 8, 152 * 16);
-  const int pgrid = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
-  count_launches(2);
-  if (total < (int64_t(1) << 32)) {
-    k_oz_rowexp<uint32_t><<<rgrid, 256, 0, st>>>(src, g, (uint32_t)K, (uint32_t)rows, exps);
-    k_oz_pack<uint32_t><<<pgrid, 256, 0, st>>>(src, g, (uint32_t)K, (uint32_t)total, exps, Kp, rows_p * Kp,
-                                               (__nv_bfloat16*)buf);
-  } else {
-    k_oz_rowexp<uint64_t><<<rgrid, 256, 0, st>>>(src, g, (uint64_t)K, (uint64_t)rows, exps);
-    k_oz_pack<uint64_t><<<pgrid, 256, 0, st>>>(src, g, (uint64_t)K, (uint64_t)total, exps, Kp, rows_p * Kp,
-                                               (__nv_bfloat16*)buf);
-  }
+  // the trailing dims whose extents multiply to K index K, the leading ones the rows
+  int dk = g.ndim;
+  for (int64_t prod = 1; dk > 0 && prod < K;) prod *= g.ext[--dk];
+  int64_t* off = (int64_t*)dev_alloc((size_t)(rows + K) * sizeof(int64_t), st, true);
+  int64_t k_inner = -1, r_inner = -1;
+  for (int d = g.ndim - 1; d >= dk; --d)
+    if (g.ext[d] > 1) {
+      k_inner = g.s1[d];
+      break;
+    }
+  for (int d = dk - 1; d >= 0; --d)
+    if (g.ext[d] > 1) {
+      r_inner = g.s1[d];
+      break;
+    }
+  const int along_rows = (k_inner != 1 && r_inner == 1) ? 1 : 0;
+  const int64_t ntiles = (rows_p / 32) * (Kp / 64);
+  count_launches(4);
+  k_oz_offsets<<<(int)std::min<int64_t>((rows + 255) / 256, 152 * 8), 256, 0, st>>>(g, 0, dk, rows, off);
+  k_oz_offsets<<<(int)std::min<int64_t>((K + 255) / 256, 152 * 8), 256, 0, st>>>(g, dk, g.ndim, K, off + rows);
+  k_oz_rowexp<<<(int)std::min<int64_t>((rows + 7) / 8, 152 * 16), 256, 0, st>>>(src, off, off + rows, K, rows, exps);
+  k_oz_pack<<<(int)std::min<int64_t>(ntiles, 152 * 16), 256, 0, st>>>(src, off, off + rows, rows, K, rows_p, Kp,
+                                                                      along_rows, exps, (__nv_bfloat16*)buf);
+  dev_free(off, st, true);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw std::runtime_error(std::string("oz::pack launch: ") + cudaGetErrorString(e));
 }

@@ -881,6 +881,20 @@ __global__ void k_branching_plane(int n, double gap, const double* __restrict__ 
 }
 }  // namespace
 
+__global__ void k_antisymmetric_part(int n, const double* __restrict__ D, double* __restrict__ out) {
+  const int64_t nn = (int64_t)n * n;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nn; x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = x / n, q = x % n;
+    out[x] = 0.5 * (D[x] - D[q * n + p]);
+  }
+}
+
+void launch_antisymmetric_part(int n, const double* D, double* out, cudaStream_t st) {
+  const int64_t nn = (int64_t)n * n;
+  count_launches(1);
+  k_antisymmetric_part<<<(int)std::min<int64_t>((nn + 255) / 256, 152 * 8), 256, 0, st>>>(n, D, out);
+}
+
 void launch_branching_plane(int n, double gap, const double* gk, const double* gl, const double* f, double* out,
                             cudaStream_t st) {
   count_launches(1);

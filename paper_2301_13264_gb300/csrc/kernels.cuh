@@ -81,6 +81,9 @@ void launch_argmaxabs(int64_t n, const double* x, double* out, double* work, cud
 // t-eta first term: <L|tau_sigma|(r0 + R)> for all packed sigma (see capi.cpp).
 void launch_tau_expectation(const VecShape& s, double r0, const double* L, const double* R, double* y,
                             cudaStream_t st);
+// out[p][q] = (D[p][q] - D[q][p]) / 2 for an n x n matrix (out must not overlap D).
+void launch_antisymmetric_part(int n, const double* D, double* out, cudaStream_t st);
+
 // Branching plane of two states k < l from their energy gradients gk, gl and the coupling
 // f = F_kl along n directions, gap = E_l - E_k (one CTA, FP64):
 //   out[0..n)   g = gl - gk

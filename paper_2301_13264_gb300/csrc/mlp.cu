@@ -384,7 +384,9 @@ void sample(int64_t* idx, int batch, int64_t n, unsigned long long seed, unsigne
   k_sample<<<(batch + 255) / 256, 256, 0, st>>>(idx, batch, n, seed, step);
 }
 
-__global__ void k_features(const double* __restrict__ gov, const double* __restrict__ eps, int o, int v, float* X) {
+// first feature: x0 (a start's doubles, [i][j][a][b]) when given, else t_MP2 = -(ia|jb)/D
+__global__ void k_features(const double* __restrict__ gov, const double* __restrict__ eps, int o, int v,
+                           const double* __restrict__ x0, float* X) {
   const int64_t n = (int64_t)o * o * v * v;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const int b = (int)(e % v);
@@ -394,10 +396,16 @@ __global__ void k_features(const double* __restrict__ gov, const double* __restr
     const int j = (int)(r % o), i = (int)(r / o);
     const double g = gov[(((int64_t)i * v + a) * o + j) * v + b];  // (ia|jb)
     const double D = eps[o + a] + eps[o + b] - eps[i] - eps[j];
-    X[e * 3 + 0] = (float)(-g / D);
+    X[e * 3 + 0] = (float)(x0 ? x0[e] : -g / D);
     X[e * 3 + 1] = (float)D;
     X[e * 3 + 2] = (float)fabs(g);
   }
+}
+
+// T[e] = x[e] - X[e][0]: the correction a model is trained to predict
+__global__ void k_targets(const double* __restrict__ x, const float* __restrict__ X, int64_t n, float* T) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    T[e] = (float)(x[e] - (double)X[e * 3]);
 }
 
 __global__ void k_add_delta(double* t2, const float* delta, int64_t n) {
@@ -405,10 +413,34 @@ __global__ void k_add_delta(double* t2, const float* delta, int64_t n) {
     t2[e] += (double)delta[e];
 }
 
-void features(const double* gov, const double* eps, int o, int v, float* X, cudaStream_t st) {
+void features(const double* gov, const double* eps, int o, int v, float* X, cudaStream_t st, const double* x0) {
   const int64_t n = (int64_t)o * o * v * v;
   count_launches(1);
-  k_features<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(gov, eps, o, v, X);
+  k_features<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(gov, eps, o, v, x0, X);
+}
+
+__global__ void k_mp2_doubles(const double* __restrict__ gov, const double* __restrict__ eps, int o, int v,
+                              double* __restrict__ t2) {
+  const int64_t n = (int64_t)o * o * v * v;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e % v);
+    int64_t r = e / v;
+    const int a = (int)(r % v);
+    r /= v;
+    const int j = (int)(r % o), i = (int)(r / o);
+    t2[e] = -gov[(((int64_t)i * v + a) * o + j) * v + b] / (eps[o + a] + eps[o + b] - eps[i] - eps[j]);
+  }
+}
+
+void mp2_doubles(const double* gov, const double* eps, int o, int v, double* t2, cudaStream_t st) {
+  const int64_t n = (int64_t)o * o * v * v;
+  count_launches(1);
+  k_mp2_doubles<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(gov, eps, o, v, t2);
+}
+
+void targets(const double* x, const float* X, int64_t n, float* T, cudaStream_t st) {
+  count_launches(1);
+  k_targets<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, st>>>(x, X, n, T);
 }
 
 void add_delta(double* t2, const float* delta, int64_t n, cudaStream_t st) {

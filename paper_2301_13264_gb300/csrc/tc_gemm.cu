@@ -11,16 +11,18 @@
 // its third coordinate, so the products are simply more K iterations of the
 // same mainloop.
 //
-// Kernel: one 128 x BN output tile per CTA (BN = 64, 128 or 256), 4 warps.  Warp 0
-// lane 0 issues TMA loads into a 4- or 6-stage ring (mbarrier full/empty pairs),
-// warp 1 lane 0 issues tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulate,
-// 128 x BN x 16 per instruction) and commits each stage back to the producer;
-// after the last commit all four warps read the accumulator with tcgen05.ld
-// (warp w owns TMEM lanes 32w..32w+31) and add alpha * acc into the FP64 output.
-// When the output has few tiles the K iterations are split over blockIdx.z and
-// the partial tiles are summed in FP64 by a second kernel.  Every mbarrier wait
-// is bounded; on timeout the kernel raises a device error flag, drains its own
-// copies and MMAs (bounded), frees TMEM and exits.
+// Kernel (persistent, warp-specialised): at most one CTA per SM walks the work items
+// (split-K part, 128 x BN output tile; BN = 64, 128 or 256) in raster groups, so that the
+// CTAs resident at the same time share operand strips through L2.  Warp 0 lane 0 issues
+// TMA loads into a 4- or 6-stage ring (mbarrier full/empty pairs); warp 1 lane 0 issues
+// tcgen05.mma (kind::f16, bf16 inputs, FP32 accumulate, 128 x BN x 16 per instruction)
+// into one of two TMEM accumulators and commits each stage back to the producer; warps
+// 2..5 read a finished accumulator with tcgen05.ld, hand it back, and add alpha * acc
+// into the FP64 output while the next item's products accumulate in the other one.
+// When the output has few tiles the K iterations are split, and the partial tiles are
+// summed in FP64 by a second kernel.  Every mbarrier wait is bounded; on timeout the
+// kernel raises a device error flag, drains its own copies and MMAs (bounded), frees
+// TMEM and exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -40,7 +42,7 @@ namespace ccsd {
 
 namespace tc {
 
-constexpr int NTHREADS = 128;
+constexpr int NTHREADS = 192;  // TMA warp, MMA warp, 4 epilogue warps
 constexpr int A_BYTES = BM * BK * 2;
 // per tile width BN (64, 128 or 256): B tile bytes, pipeline depth, shared memory
 template <int BN>
@@ -48,7 +50,8 @@ struct Cfg {
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int STAGES = (BN == 256) ? 4 : 6;
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  // stages, the strided-output column offsets [BN], barriers; 1 KB alignment slack
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BN * 8 + 256 + 1024;
 };
 constexpr int MAXPROD = 6;
 
@@ -56,7 +59,8 @@ struct Params {
   int M, N;
   int kt_per_prod;    // 64-wide K tiles per slice
   int nprod;
-  int it_per_split;   // K iterations per blockIdx.z
+  int it_per_split;   // K iterations per split
+  int nsplit;         // K splits: work items are (split, tile) pairs
   int pa[MAXPROD], pb[MAXPROD];
   double* C;          // nsplit == 1: output
   long long sCm, sCn;
@@ -84,33 +88,57 @@ __device__ __forceinline__ long long dim_offset(long long x, const Strided& g) {
   return off;
 }
 
+// Named barrier among the 128 epilogue threads (warps 2..5); barrier 0 is __syncthreads.
+__device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive1(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent GEMM: gridDim.x CTAs (at most one per SM) walk the work items
+// w = blockIdx.x, blockIdx.x + gridDim.x, ... of (split z, output tile) in raster order.
+// Warp 0 lane 0 loads A and B K-tiles by TMA into the STAGES-deep ring; warp 1 lane 0
+// issues the MMAs of an item into one of two TMEM accumulators (columns b*BN, b = item
+// parity) and commits acc_full[b]; warps 2..5 read the finished accumulator (warp w owns
+// TMEM lanes 32 (w % 4) ..), release it with acc_empty[b] and write the FP64 output while
+// the MMA warp already fills the other accumulator for the next item.
 template <int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, Params p) {
   constexpr int STAGES = Cfg<BN>::STAGES, B_BYTES = Cfg<BN>::B_BYTES, STAGE_BYTES = Cfg<BN>::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
+  __shared__ int s_skip;  // the error flag as thread 0 saw it: one decision for the whole CTA
   volatile int* err = p.err;
-  if (*err) return;
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
-  uint64_t* bars = (uint64_t*)(smem + STAGES * STAGE_BYTES);
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+  long long* coloff = reinterpret_cast<long long*>(smem + STAGES * STAGE_BYTES);  // [BN]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + BN * sizeof(long long));
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 5);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t accf0 = smem_u32(bars + 2 * STAGES), acce0 = smem_u32(bars + 2 * STAGES + 2);
+  const uint32_t done = smem_u32(bars + 2 * STAGES + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int tm, tn;
-  raster_tile(blockIdx.x, p.mt, p.nt, p.group_m, tm, tn);
-  const int m0 = tm * BM, n0 = tn * BN;
+  const int tiles = p.mt * p.nt;
+  const int items = tiles * p.nsplit;
   const int total = p.nprod * p.kt_per_prod;
-  const int it0 = blockIdx.z * p.it_per_split;
-  const int it1 = min(total, it0 + p.it_per_split);
-  const int iters = max(0, it1 - it0);
+  // K-iteration range of work item w (z = w / tiles)
+  auto k_range = [&](int w, int& it0, int& it1) {
+    const int z = w / tiles;
+    it0 = z * p.it_per_split;
+    it1 = min(total, it0 + p.it_per_split);
+  };
 
   if (threadIdx.x == 0) {
+    s_skip = *err;
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
+    mbar_init(accf0, 1);
+    mbar_init(accf0 + 8, 1);
+    mbar_init(acce0, 4);
+    mbar_init(acce0 + 8, 4);
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&ta)) : "memory");
@@ -118,7 +146,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(BN)
+                 "r"(2 * BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -127,105 +155,143 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0) {
+  if (s_skip) {
+    // an earlier kernel of this stream raised the flag: nothing to do but free TMEM
+  } else if (warp == 0) {
+    // ---- TMA producer ----
     if (lane == 0) {
-      int issued = 0;
+      long long issued = 0;
       bool ok = true;
-      for (int it = 0; it < (p.stall ? 0 : iters); ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, err, p.budget)) {
-          ok = false;
-          break;
-        }
-        const int g = it0 + it;
-        const int prod = g / p.kt_per_prod, kt = g % p.kt_per_prod;
-        mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-        tma_load_3d(smem_u32(sA + s * A_BYTES), &ta, full0 + 8 * s, kt * BK, m0, p.pa[prod]);
-        tma_load_3d(smem_u32(sB + s * B_BYTES), &tb, full0 + 8 * s, kt * BK, n0, p.pb[prod]);
-        ++issued;
-      }
-      if (!ok) {
-        atomicExch((int*)p.err, 1);
-        // drain this CTA's copies still in flight (bounded)
-        for (int it = issued - 1; it >= 0 && it >= issued - STAGES; --it) {
-          const int s = it % STAGES;
-          const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-          long long t0 = clock64();
-          while (!mbar_try_wait(full0 + 8 * s, ph) && clock64() - t0 < TIMEOUT_CYCLES) {
+      for (int w = blockIdx.x; ok && w < items && !p.stall; w += gridDim.x) {
+        int tm, tn, it0, it1;
+        raster_tile(w % tiles, p.mt, p.nt, p.group_m, tm, tn);
+        k_range(w, it0, it1);
+        for (int it = it0; it < it1; ++it, ++issued) {
+          const int s = (int)(issued % STAGES);
+          const uint32_t ph = (uint32_t)(issued / STAGES) & 1u;
+          if (!mbar_wait(empty0 + 8 * s, ph ^ 1u, err, p.budget)) {
+            ok = false;
+            break;
           }
+          const int prod = it / p.kt_per_prod, kt = it % p.kt_per_prod;
+          mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+          tma_load_3d(smem_u32(sA + s * A_BYTES), &ta, full0 + 8 * s, kt * BK, tm * BM, p.pa[prod]);
+          tma_load_3d(smem_u32(sB + s * B_BYTES), &tb, full0 + 8 * s, kt * BK, tn * BN, p.pb[prod]);
+        }
+      }
+      if (!ok) atomicExch((int*)p.err, 1);
+      // the copies this CTA issued last (one per stage) must land before it exits
+      for (long long it = issued - 1; it >= 0 && it >= issued - STAGES; --it) {
+        const int s = (int)(it % STAGES);
+        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+        const long long t0 = clock64();
+        while (!mbar_try_wait(full0 + 8 * s, ph) && clock64() - t0 < TIMEOUT_CYCLES) {
         }
       }
     }
     __syncwarp();
   } else if (warp == 1) {
+    // ---- MMA issuer ----
     if (lane == 0) {
+      long long consumed = 0;
+      int item = 0;
       bool ok = true;
-      for (int it = 0; it < iters; ++it) {
-        const int s = it % STAGES;
-        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-        if (!mbar_wait(full0 + 8 * s, ph, err, p.budget)) {
+      for (int w = blockIdx.x; ok && w < items; w += gridDim.x, ++item) {
+        int it0, it1;
+        k_range(w, it0, it1);
+        const int b = item & 1;
+        const uint32_t use = (uint32_t)(item >> 1) & 1u;
+        if (!mbar_wait(acce0 + 8 * b, use ^ 1u, err, p.budget)) {
           ok = false;
           break;
         }
         fence_after();
-        const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
+        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        for (int it = it0; it < it1; ++it, ++consumed) {
+          const int s = (int)(consumed % STAGES);
+          const uint32_t ph = (uint32_t)(consumed / STAGES) & 1u;
+          if (!mbar_wait(full0 + 8 * s, ph, err, p.budget)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          const uint32_t a0 = smem_u32(sA + s * A_BYTES), b0 = smem_u32(sB + s * B_BYTES);
 #pragma unroll
-        for (int j = 0; j < BK / 16; ++j)
-          mma_bf16(tmem, smem_desc(a0 + 32 * j), smem_desc(b0 + 32 * j), idesc<BN>(), (it | j) != 0 ? 1u : 0u);
-        mma_commit(empty0 + 8 * s);
+          for (int j = 0; j < BK / 16; ++j)
+            mma_bf16(acc, smem_desc(a0 + 32 * j), smem_desc(b0 + 32 * j), idesc<BN>(), (it != it0 || j != 0) ? 1u : 0u);
+          mma_commit(empty0 + 8 * s);
+        }
+        if (!ok) break;
+        mma_commit(accf0 + 8 * b);  // fires once the item's MMAs have completed
       }
       if (!ok) atomicExch((int*)p.err, 1);
-      mma_commit(done);  // fires once every issued MMA has completed
+      // every MMA this thread issued completes before the accumulators are freed
+      mma_commit(done);
+      const long long t0 = clock64();
+      while (!mbar_try_wait(done, 0) && clock64() - t0 < TIMEOUT_CYCLES) {
+      }
     }
     __syncwarp();
-  }
-
-  // epilogue: TMEM -> registers -> FP64 output (or FP64 partial tile)
-  const bool ready = mbar_wait(done, 0, err);
-  fence_after();
-  if (!ready) atomicExch((int*)p.err, 1);
-  const bool split = (gridDim.z > 1);
-  const bool ostr = !split && p.ostr;
-  // strided output: the tile's column offsets, computed once into the stage
-  // buffers (idle once the done barrier has fired: every MMA and every copy
-  // feeding it has completed)
-  long long* coloff = reinterpret_cast<long long*>(sA);
-  if (ostr && ready)
-    for (int c = threadIdx.x; c < BN; c += NTHREADS) coloff[c] = (n0 + c < p.N) ? dim_offset(n0 + c, p.on) : 0;
-  __syncthreads();
-  if (ready && !*err && iters > 0) {
-    const int row = m0 + warp * 32 + lane;
-    double* crow = split ? p.part + ((long long)blockIdx.z * p.M + row) * p.N
-                         : (ostr ? p.C + (row < p.M ? dim_offset(row, p.om) : 0) : p.C + (long long)row * p.sCm);
-    const long long cs = split ? 1 : p.sCn;
+  } else {
+    // ---- epilogue: warps 2..5, TMEM lanes 32 (warp % 4) ----
+    const int lane_base = 32 * (warp & 3);
+    const int et = threadIdx.x - 64;  // 0..127
+    int item = 0;
+    for (int w = blockIdx.x; w < items; w += gridDim.x, ++item) {
+      int tm, tn, it0, it1;
+      raster_tile(w % tiles, p.mt, p.nt, p.group_m, tm, tn);
+      k_range(w, it0, it1);
+      const int z = w / tiles;
+      const int m0 = tm * BM, n0 = tn * BN;
+      const int b = item & 1;
+      const uint32_t use = (uint32_t)(item >> 1) & 1u;
+      const bool split = p.nsplit > 1;
+      const bool ostr = !split && p.ostr;
+      // column offsets of a strided output for this tile (the previous tile's are no longer read)
+      epilogue_sync();
+      if (ostr)
+        for (int c = et; c < BN; c += 128) coloff[c] = (n0 + c < p.N) ? dim_offset(n0 + c, p.on) : 0;
+      epilogue_sync();
+      // the accumulator wait spans the item's whole mainloop: default bound.  On failure the
+      // four warps do not leave the loop (they would then disagree on the named barriers
+      // above): they keep walking the items with every wait failing fast on the raised flag.
+      const bool ready = mbar_wait(accf0 + 8 * b, use, err);
+      if (!ready) atomicExch((int*)p.err, 1);
+      fence_after();
+      const int row = m0 + lane_base + lane;
+      double* crow = split ? p.part + ((long long)z * p.M + row) * p.N
+                           : (ostr ? p.C + (row < p.M ? dim_offset(row, p.om) : 0) : p.C + (long long)row * p.sCm);
+      const long long cs = split ? 1 : p.sCn;
+      const bool empty = it1 <= it0 || !ready;
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
-      if (row < p.M) {
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        if (!empty) tmem_ld32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(b * BN + c), r);
+        if (c + 32 >= BN) {
+          // every load of this accumulator has completed: hand it back to the MMA warp
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive1(acce0 + 8 * b);
+        }
+        if (ready && row < p.M && !*err) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = n0 + c + j;
-          if (n < p.N) {
-            double* dst = crow + (ostr ? coloff[c + j] : (long long)n * cs);
-            const double v = p.alpha * (double)__uint_as_float(r[j]);
-            *dst = (split || p.beta_zero) ? v : (*dst + v);
+          for (int j = 0; j < 32; ++j) {
+            const int n = n0 + c + j;
+            if (n < p.N) {
+              double* dst = crow + (ostr ? coloff[c + j] : (long long)n * cs);
+              const double v = empty ? 0.0 : p.alpha * (double)__uint_as_float(r[j]);
+              *dst = (split || p.beta_zero) ? v : (*dst + v);
+            }
           }
         }
       }
     }
-  } else if (ready && !*err && gridDim.z > 1) {
-    // an empty K range still owns its partial tile: write zeros
-    const int row = m0 + warp * 32 + lane;
-    if (row < p.M)
-      for (int n = n0; n < min(p.N, n0 + BN); ++n) p.part[((long long)blockIdx.z * p.M + row) * p.N + n] = 0.0;
   }
   fence_before();
   __syncthreads();
   fence_after();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN) : "memory");
   }
 }
 
@@ -243,29 +309,73 @@ __global__ void k_tc_reduce(int M, int N, int nsplit, const double* __restrict__
   }
 }
 
-// FP64 strided gather -> S bf16 slices, dst[s][row][Kp] with row-major (rows, K)
-// coordinates decomposed over the index space g (its leading dims index rows,
-// its trailing dims index K; g.s1 are the source strides).
-template <typename I>
-__global__ void k_split_pack(const double* __restrict__ src, Strided g, I K, I total, int S, int64_t Kp,
-                             int64_t plane, __nv_bfloat16* __restrict__ dst) {
-  for (I idx = (I)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (I)gridDim.x * blockDim.x) {
-    I r = idx;
-    int64_t off = 0;
-    for (int d = g.ndim - 1; d >= 0; --d) {
-      const I e = (I)g.ext[d];
-      const I c = r % e;
+// Offsets of a strided gather split into its leading (row) dims and its trailing (K)
+// dims: off[x] = sum over dims d in [d0, d1) of coord_d(x) * g.s1[d], x decomposed
+// row-major over those dims' extents.  One thread per entry.
+__global__ void k_gather_offsets(Strided g, int d0, int d1, int64_t n, int64_t* __restrict__ off) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = x, o = 0;
+    for (int d = d1 - 1; d >= d0; --d) {
+      const int64_t e = g.ext[d];
+      o += (r % e) * g.s1[d];
       r /= e;
-      off += (int64_t)c * g.s1[d];
     }
-    const I row = idx / K, k = idx % K;
-    double x = src[off];
-    __nv_bfloat16* dd = dst + (int64_t)row * Kp + k;
-    for (int s = 0; s < S; ++s) {
-      __nv_bfloat16 b = __double2bfloat16(x);
-      dd[s * plane] = b;
-      x -= (double)__bfloat162float(b);
+    off[x] = o;
+  }
+}
+
+// FP64 gather -> S bf16 slices dst[s][row][Kp] (rows_p x Kp, padding zero), element
+// (row, k) read at src[rowoff[row] + koff[k]].  Tiles of 32 rows x 64 k through shared
+// memory: along_rows = 0 reads consecutive k per warp (the source is contiguous along
+// K), along_rows = 1 reads consecutive rows (contiguous along the rows) and transposes;
+// the slices are written as bf16 pairs along k.
+__global__ void __launch_bounds__(256) k_split_gather(const double* __restrict__ src, const int64_t* __restrict__ rowoff,
+                                                      const int64_t* __restrict__ koff, int64_t rows, int64_t K,
+                                                      int64_t rows_p, int64_t Kp, int S, int along_rows,
+                                                      __nv_bfloat16* __restrict__ dst) {
+  __shared__ double tile[32][65];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t ktiles = Kp / 64, ntiles = (rows_p / 32) * ktiles;
+  const int64_t plane = rows_p * Kp;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = (t / ktiles) * 32, k0 = (t % ktiles) * 64;
+    if (along_rows) {
+      const int64_t r = r0 + tx;
+      const int64_t ro = r < rows ? rowoff[r] : 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int kk = ty + 8 * i;
+        const int64_t k = k0 + kk;
+        tile[tx][kk] = (r < rows && k < K) ? src[ro + koff[k]] : 0.0;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int rr = ty + 8 * i;
+        const int64_t r = r0 + rr;
+        const int64_t ro = r < rows ? rowoff[r] : 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int kk = tx + 32 * h;
+          const int64_t k = k0 + kk;
+          tile[rr][kk] = (r < rows && k < K) ? src[ro + koff[k]] : 0.0;
+        }
+      }
     }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int rr = ty + 8 * i;
+      double x0 = tile[rr][2 * tx], x1 = tile[rr][2 * tx + 1];
+      __nv_bfloat162* d = reinterpret_cast<__nv_bfloat162*>(dst + (r0 + rr) * Kp + k0 + 2 * tx);
+      for (int s = 0; s < S; ++s) {
+        const __nv_bfloat16 b0 = __double2bfloat16(x0), b1 = __double2bfloat16(x1);
+        d[s * (plane / 2)] = __halves2bfloat162(b0, b1);
+        x0 -= (double)__bfloat162float(b0);
+        x1 -= (double)__bfloat162float(b1);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -376,22 +486,50 @@ int Executor::tc_error() {
 }
 
 // bf16 slices [S][rows_p][Kp] of an FP64 operand given as a strided gather over
-// (row dims..., K dims...); padding rows and columns are zero.
+// (row dims..., K dims...); padding rows and columns are zero.  rows_p is a multiple of
+// 128 and Kp of 64, so the 32 x 64 tiles of the gather cover the array exactly.
 static __nv_bfloat16* make_slices(cudaStream_t st, const double* src, const Strided& g, int64_t rows, int64_t rows_p,
                                   int64_t K, int S, int64_t Kp) {
   size_t bytes = (size_t)S * rows_p * Kp * sizeof(__nv_bfloat16);
   void* p = dev_alloc(bytes, st, true);
-  if (Kp != K || rows_p != rows) cudaMemsetAsync(p, 0, bytes, st);
-  const int64_t total = rows * K;
-  const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
-  count_launches(1);
-  if (total < (int64_t(1) << 32))
-    tc::k_split_pack<uint32_t><<<grid, 256, 0, st>>>(src, g, (uint32_t)K, (uint32_t)total, S, Kp, rows_p * Kp,
-                                                     (__nv_bfloat16*)p);
-  else
-    tc::k_split_pack<uint64_t><<<grid, 256, 0, st>>>(src, g, (uint64_t)K, (uint64_t)total, S, Kp, rows_p * Kp,
-                                                     (__nv_bfloat16*)p);
+  // the trailing dims whose extents multiply to K index K, the leading ones the rows
+  int dk = g.ndim;
+  for (int64_t prod = 1; dk > 0 && prod < K;) prod *= g.ext[--dk];
+  int64_t* off = (int64_t*)dev_alloc((size_t)(rows + K) * sizeof(int64_t), st, true);
+  count_launches(3);
+  tc::k_gather_offsets<<<(int)std::min<int64_t>((rows + 255) / 256, 152 * 8), 256, 0, st>>>(g, 0, dk, rows, off);
+  tc::k_gather_offsets<<<(int)std::min<int64_t>((K + 255) / 256, 152 * 8), 256, 0, st>>>(g, dk, g.ndim, K, off + rows);
+  // read along whichever side is contiguous in the source
+  int64_t k_inner = -1, r_inner = -1;
+  for (int d = g.ndim - 1; d >= dk; --d)
+    if (g.ext[d] > 1) {
+      k_inner = g.s1[d];
+      break;
+    }
+  for (int d = dk - 1; d >= 0; --d)
+    if (g.ext[d] > 1) {
+      r_inner = g.s1[d];
+      break;
+    }
+  const int along_rows = (k_inner != 1 && r_inner == 1) ? 1 : 0;
+  const int64_t ntiles = (rows_p / 32) * (Kp / 64);
+  tc::k_split_gather<<<(int)std::min<int64_t>(ntiles, 152 * 16), 256, 0, st>>>(
+      src, off, off + rows, rows, K, rows_p, Kp, S, along_rows, (__nv_bfloat16*)p);
+  dev_free(off, st, true);
   return (__nv_bfloat16*)p;
+}
+
+// multiprocessors of the current device (queried once per device)
+static int sm_count() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (!cached[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 152;
+    cached[dev] = n;
+  }
+  return cached[dev];
 }
 
 template <int BN>
@@ -636,7 +774,11 @@ void Executor::tc_run(const void* a, int64_t Mp, const void* b, int64_t Np, int 
   p.mt = (int)(Mp / tc::BM);
   p.nt = (int)(Np / BN);
   p.group_m = tc::raster_group(p.mt, BN);
-  dim3 grid((unsigned)(p.mt * p.nt), 1u, (unsigned)nsplit);
+  p.nsplit = nsplit;
+  if ((int64_t)p.mt * p.nt * nsplit > (int64_t)INT32_MAX) throw std::runtime_error("tc_run: too many work items");
+  // persistent: at most one CTA per SM walks the (split, tile) work items
+  const int items = p.mt * p.nt * nsplit;
+  dim3 grid((unsigned)std::min(items, sm_count()), 1u, 1u);
   last_tc_issued = 2.0 * (double)Mp * (double)Np * (double)Kp * p.nprod;
   if (BN == 256)
     launch_tc<256>(grid, ta, tb, p, st_);

@@ -178,3 +178,53 @@ def test_thymine_adz_transform_properties():
         assert float((fd - AR[0]).abs().max() / AR[0].abs().max()) < 1e-4
     finally:
         B.ccsd_destroy(h64)
+
+
+def _golden_adz():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "thymine_adz_transforms.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_thymine_adz_transforms_match_oracle_samples(precision):
+    """o=33, v=228, naux=900 at the benchmark's launch configuration: one right and one
+    left transform against the oracle's full FP64 transforms, stored by
+    tests/golden/make_thymine_adz_transforms.py (4160 sampled elements including the 64
+    largest, plus the largest magnitude, packed norm and sum over all 5.66e7 elements).
+    Three-slice products: within 2e-5 of the largest element; FP64: 1e-11."""
+    G = _golden_adz()
+    H = workload("thymine_adz")
+    o, v = H.o, H.v
+    X1, X2 = random_amplitudes(o, v, 22, scale=0.01, nvec=3)
+    t = torch.as_tensor(flat(X1[0], X2[0]), device="cuda")
+    R = torch.as_tensor(flat(X1[1], X2[1]), device="cuda")[None].contiguous()
+    L = torch.as_tensor(flat(X1[2], X2[2]), device="cuda")[None].contiguous()
+    opt = (B.ccsd_default_options(precision=B.PREC_MIXED, splits=3) if precision == "mixed"
+           else B.ccsd_default_options())
+    tol = TOL[3] if precision == "mixed" else 1e-11
+    h = B.ccsd_create(H.eps, H.h, H.B, o, v, H.naux, opt)
+    try:
+        B.ccsd_set_amplitudes(h, t, torch.zeros_like(t))
+        out = {}
+        for side, X in (("right", R), ("left", L)):
+            Y = torch.zeros_like(X)
+            B.ccsd_jacobian_transform(h, 0 if side == "right" else 1, 1, X, Y)
+            out[side] = Y[0]
+    finally:
+        B.ccsd_destroy(h)
+    w = torch.as_tensor(cc.pair_weight(o, v).numpy().reshape(-1), device="cuda")
+    n1 = o * v
+    for side, y in out.items():
+        g = G[side]
+        idx = torch.as_tensor(g["index"], device="cuda")
+        ref = np.array(g["value"])
+        got = y[idx].cpu().numpy()
+        assert np.abs(got - ref).max() < tol * g["maxabs"], side
+        assert abs(float(y.abs().max()) - g["maxabs"]) < tol * g["maxabs"]
+        pn = float(((y[:n1] * y[:n1]).sum() + (w * y[n1:] * y[n1:]).sum()).sqrt())
+        assert abs(pn - g["packed_norm"]) < tol * g["packed_norm"]
+        # the plain sum over 5.66e7 elements cancels: bound by the per-element error times the count
+        assert abs(float(y.sum()) - g["sum"]) < tol * g["maxabs"] * y.numel() ** 0.5 * 10
