@@ -308,11 +308,13 @@ def run_ours(args, rank, world, local_rank):
     B.ccsd_profile_start(h)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler select the timed steps (ncu --nvtx-include timed/)
     ev0.record(stream)
     for _ in range(args.steps):
         step()
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     prof = B.ccsd_profile_stop(h)
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)

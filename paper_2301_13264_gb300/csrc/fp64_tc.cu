@@ -380,28 +380,64 @@ __global__ void k_oz_offsets(Strided g, int d0, int d1, int64_t n, int64_t* __re
 }
 
 // one warp per row: e_r with max_k |X_rk| < 2^e_r (0 for a zero row, NONFINITE for Inf/NaN);
-// element (row, k) at src[rowoff[row] + koff[k]]
+// element (row, k) at src[rowoff[row] + koff[k]].  Integer operations on the bit patterns
+// (for finite values the order of |x| is the order of their sign-cleared patterns), so the
+// pass does not queue on the FP64 pipe.
 __global__ void k_oz_rowexp(const double* __restrict__ src, const int64_t* __restrict__ rowoff,
                             const int64_t* __restrict__ koff, int64_t K, int64_t rows, int* __restrict__ exps) {
   const int lane = threadIdx.x & 31;
   const int64_t wpb = blockDim.x >> 5;
+  const unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
   for (int64_t row = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); row < rows; row += (int64_t)gridDim.x * wpb) {
     const int64_t ro = rowoff[row];
-    double m = 0.0;
-    bool finite = true;
-    for (int64_t k = lane; k < K; k += 32) {
-      const double x = fabs(src[ro + koff[k]]);
-      if (!(x <= 1.7976931348623157e308)) finite = false;
-      else m = fmax(m, x);
-    }
+    unsigned long long m = 0;
+    for (int64_t k = lane; k < K; k += 32) m = max(m, (unsigned long long)__double_as_longlong(src[ro + koff[k]]) & kAbs);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    finite = __all_sync(0xffffffffu, finite);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) {
       int e = 0;
-      if (m > 0.0) frexp(m, &e);
-      exps[row] = finite ? e : NONFINITE;
+      if (m >= kInf) {
+        e = NONFINITE;
+      } else if (m != 0) {
+        const int E = (int)(m >> 52);
+        // |x| = 1.f 2^(E - 1023) = 0.1f 2^(E - 1022) < 2^(E - 1022); subnormals: below 2^-1022
+        e = (E > 0) ? E - 1022 : -1022;
+      }
+      exps[row] = e;
     }
+  }
+}
+
+// bf16 bit pattern of q * 2^(-7 s) for an integer |q| <= 64 (exact: at most 7 significant bits)
+__device__ __forceinline__ unsigned short oz_slice_bits(long long q, int s) {
+  if (q == 0) return 0;
+  const unsigned int sign = q < 0 ? 0x8000u : 0u;
+  const unsigned int a = (unsigned int)(q < 0 ? -q : q);
+  const int p = 31 - __clz(a);  // a in [2^p, 2^(p+1))
+  const unsigned int mant = (a << (7 - p)) & 0x7Fu;
+  return (unsigned short)(sign | ((unsigned int)(127 + p - 7 * s) << 7) | mant);
+}
+
+// The 7 slices of x in a row with exponent e: y = x 2^(6 - e) (|y| < 64) held as the fixed-point
+// integer Y = y 2^56 (|Y| < 2^62; bits of y below 2^-56 are dropped, far below the 2^-42 of
+// the last slice), then q_s = round(Y / 2^56) (half up: |y - q_s| <= 1/2, so |q_s| <= 64 at
+// every step) and Y = (Y - q_s 2^56) 128.  Integer operations only.  Subnormal inputs count as
+// zero.
+__device__ __forceinline__ void oz_slices(double x, int e, unsigned short (&out)[S]) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((u >> 52) & 0x7FFu);
+  long long Y = 0;
+  if (e != NONFINITE && E != 0) {
+    const long long M = (long long)((u & ((1ull << 52) - 1)) | (1ull << 52));
+    const int sh = E - 1013 - e;  // Y = M 2^sh; sh <= 9 because |x| < 2^e
+    Y = sh >= 0 ? (M << sh) : (sh > -63 ? (M >> -sh) : 0);
+    if (u >> 63) Y = -Y;
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const long long q = (Y + (1ll << 55)) >> 56;
+    out[s] = oz_slice_bits(q, s);
+    Y = (Y - (q << 56)) * 128;
   }
 }
 
@@ -447,17 +483,12 @@ __global__ void __launch_bounds__(256) k_oz_pack(const double* __restrict__ src,
       const int rr = ty + 8 * i;
       const int64_t r = r0 + rr;
       const int e = r < rows ? exps[r] : NONFINITE;
-      double y0 = (e == NONFINITE) ? 0.0 : ldexp(tile[rr][2 * tx], 6 - e);  // |y| < 64
-      double y1 = (e == NONFINITE) ? 0.0 : ldexp(tile[rr][2 * tx + 1], 6 - e);
-      __nv_bfloat162* d = reinterpret_cast<__nv_bfloat162*>(dst + r * Kp + k0 + 2 * tx);
+      unsigned short q0[S], q1[S];
+      oz_slices(tile[rr][2 * tx], e, q0);
+      oz_slices(tile[rr][2 * tx + 1], e, q1);
+      unsigned int* d = reinterpret_cast<unsigned int*>(dst + r * Kp + k0 + 2 * tx);
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        const double q0 = rint(y0), q1 = rint(y1);  // integers in [-64, 64]
-        d[s * (plane / 2)] = __halves2bfloat162(__double2bfloat16(ldexp(q0, -7 * s)),  // exact in bf16
-                                                __double2bfloat16(ldexp(q1, -7 * s)));
-        y0 = (y0 - q0) * 128.0;  // exact; |y| <= 64
-        y1 = (y1 - q1) * 128.0;
-      }
+      for (int s = 0; s < S; ++s) d[s * (plane / 2)] = (unsigned int)q0[s] | ((unsigned int)q1[s] << 16);
     }
     __syncthreads();
   }

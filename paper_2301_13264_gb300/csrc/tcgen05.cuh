@@ -131,6 +131,29 @@ inline int raster_group(int mt, int bn) {
   return mt < g ? mt : g;
 }
 
+// Round-to-nearest-even conversion of a double to float with integer operations only, so
+// that operand packing does not queue on the FP64 pipe (a few lanes per SM on this chip).
+// Values below the float normal range flush to a signed zero; overflow gives infinity;
+// NaN stays NaN.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int sign = (unsigned int)(u >> 63) << 31;
+  const int e = (int)((u >> 52) & 0x7FFu);
+  const unsigned long long m = u & ((1ull << 52) - 1);
+  if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
+  int ef = e - 1023 + 127;
+  if (e == 0 || ef <= 0) return __uint_as_float(sign);
+  unsigned long long keep = m >> 29;
+  const unsigned long long rest = m & ((1ull << 29) - 1), half = 1ull << 28;
+  if (rest > half || (rest == half && (keep & 1ull))) ++keep;
+  if (keep == (1ull << 23)) {
+    keep = 0;
+    ++ef;
+  }
+  if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned int)ef << 23) | (unsigned int)keep);
+}
+
 // 3-D TMA map over bf16 slices [S][rows][Kp]: boxes of 64 K x box_rows rows x 1 slice,
 // 128-byte swizzle (tc_gemm.cu)
 CUtensorMap make_map(const void* base, int64_t rows, int64_t Kp, int S, int box_rows);
