@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--ttc", default=None,
                     help="instead of transform throughput, time create -> ground -> EOM (2 roots) -> couplings "
                          "for the comma-separated forms among mixed, fp64, fp64tc ('both' = mixed,fp64)")
+    ap.add_argument("--tol-eom", type=float, default=1e-8, help="--ttc: EOM residual-norm threshold")
+    ap.add_argument("--max-sub", type=int, default=48, help="--ttc: Davidson subspace size before a restart")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of the single-system bench, time batched transforms of this many small systems")
     ap.add_argument("--no-autotune", action="store_true", help="batch mode: tile widths from the output width")
@@ -435,7 +437,9 @@ DTYPE = {0: "f64", 1: "f64 (bf16x%d split tensor-core products, fp32 accumulate)
 def run_ttc(args):
     """Time-to-converged coupling: wall time from ccsd_create through the
     derivative couplings F_12, F_01, F_20 along (h1, B1), per precision form, at
-    the same convergence thresholds (1e-10 residual, 1e-8 EOM, 1e-9 linear)."""
+    the same convergence thresholds (1e-10 residual, --tol-eom (1e-8) EOM, 1e-9
+    linear).  Every form is compared, root by root, with the FP64 DFMA form when
+    it ran, else with the FP64-grade tensor-core form."""
     import torch
     from paper_2301_13264_gb300 import binding as B
     from paper_2301_13264_gb300.synth import workload
@@ -450,8 +454,8 @@ def run_ttc(args):
            "forms": {}}
     for form in forms:
         prec = precision_of(form)
-        opt = B.ccsd_default_options(precision=prec, splits=args.splits, tol_res=1e-10, tol_eom=1e-8,
-                                     tol_lin=1e-9, max_iter=200, refine=1)
+        opt = B.ccsd_default_options(precision=prec, splits=args.splits, tol_res=1e-10, tol_eom=args.tol_eom,
+                                     tol_lin=1e-9, max_iter=300, refine=1, davidson_max_sub=args.max_sub)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = B.ccsd_create(H.eps, H.h, H.B, H.o, H.v, H.naux, opt)
@@ -470,14 +474,20 @@ def run_ttc(args):
                               "e_ccsd": e, "omega": w, "F": F, "iters": [it_g, it_r, it_l],
                               "stats": B.ccsd_stats(h)}
         B.ccsd_destroy(h)
-    if "fp64" in out["forms"]:
-        f = out["forms"]["fp64"]
+    out["thresholds"] = {"tol_res": 1e-10, "tol_eom": args.tol_eom, "tol_lin": 1e-9, "davidson_max_sub": args.max_sub}
+    ref_name = "fp64" if "fp64" in out["forms"] else ("fp64tc" if "fp64tc" in out["forms"] else None)
+    if ref_name:
+        f = out["forms"][ref_name]
+        out["reference_form"] = ref_name
         for name, m in out["forms"].items():
-            if name == "fp64":
+            if name == ref_name:
                 continue
-            m["vs_fp64"] = {"speedup": f["seconds"] / m["seconds"], "energy_diff": abs(m["e_ccsd"] - f["e_ccsd"]),
-                            "omega_diff": max(abs(a - b) for a, b in zip(m["omega"], f["omega"])),
-                            "coupling_rel_diff": max(abs(a - b) / abs(b) for a, b in zip(m["F"], f["F"]))}
+            m["vs_" + ref_name] = {
+                "speedup": f["seconds"] / m["seconds"], "energy_diff": abs(m["e_ccsd"] - f["e_ccsd"]),
+                "omega_diff_per_root": [abs(a - b) for a, b in zip(m["omega"], f["omega"])],
+                "coupling_rel_diff_per_pair": [abs(a - b) / abs(b) for a, b in zip(m["F"], f["F"])],
+                "omega_diff": max(abs(a - b) for a, b in zip(m["omega"], f["omega"])),
+                "coupling_rel_diff": max(abs(a - b) / abs(b) for a, b in zip(m["F"], f["F"]))}
     print(json.dumps(out), flush=True)
 
 

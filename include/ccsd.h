@@ -191,6 +191,20 @@ ccsd_status ccsd_gradient_densities(ccsd_handle h, int k, double* D, double* Z);
  * sum_pq D_pq dh_pq + sum_Jpq Z_Jpq dB_Jpq with the densities of ccsd_gradient_densities. */
 ccsd_status ccsd_energy_gradient(ccsd_handle h, int k, int ndir, const double* dh, const double* dB, double* g);
 
+/* Normalisation factor of a left state (Implementation; Numerical examples, the comparison
+ * with full CI): N_k^L = 1/|psi_k^L| with <psi_k^L| = <HF|(l0 + L_k) exp(-T) (k = 0: the
+ * ground state's left state, l0 = 1 and L = Lambda).  The left state has no component beyond
+ * the doubles, so the norm is exact: a_0^2 plus the metric of the biorthonormal bras applied
+ * to a_mu = <psi^L|tau_mu|HF>, a_0 = <psi^L|HF>. */
+ccsd_status ccsd_left_norm(ccsd_handle h, int k, double* N);
+
+/* The normalised, antisymmetrised coupling of the paper's comparison with normalised (full
+ * CI) states, with N^R approximated by 1/N^L:
+ * F[d] = (N_k^L / N_l^L F_kl - N_l^L / N_k^L F_lk) / 2 along ndir directions (as
+ * ccsd_derivative_coupling; k != l). */
+ccsd_status ccsd_normalized_coupling(ccsd_handle h, int k, int l, int ndir, const double* dh, const double* dB,
+                                     double* F);
+
 /* One-electron transition density D[n*n], D_pq = <psi_k^L| E_pq |psi_l^R> at the solved
  * states (k != l; k, l = 0 the ground state), the density the orbital-connection term and
  * the orbital multipliers are built from (section on orbital connections; Implementation,

@@ -245,6 +245,18 @@ def ccsd_branching_plane(h, k, l, ndir, dh, dB):
     return v[:ndir], v[ndir:2 * ndir], v[2 * ndir:]
 
 
+def ccsd_left_norm(h, k):
+    N = ctypes.c_double()
+    _check(h, lib().ccsd_left_norm(h, k, ctypes.byref(N)))
+    return N.value
+
+
+def ccsd_normalized_coupling(h, k, l, ndir, dh, dB):
+    F = (ctypes.c_double * ndir)()
+    _check(h, lib().ccsd_normalized_coupling(h, k, l, ndir, _ptr(dh), _ptr(dB), F))
+    return list(F)
+
+
 def ccsd_transition_density(h, k, l, D):
     _check(h, lib().ccsd_transition_density(h, k, l, _ptr(D)))
 

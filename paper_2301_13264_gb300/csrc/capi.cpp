@@ -1771,6 +1771,9 @@ ccsd_status ccsd_derivative_coupling(ccsd_handle c, int k, int l, int ndir, cons
   });
 }
 
+}  // extern "C"
+
+namespace {
 // checks of the state indices of a transition density (k, l) and the states it needs
 void check_pair(ccsd_ctx* c, int k, int l) {
   const int nr = (int)c->omega.size();
@@ -1779,6 +1782,10 @@ void check_pair(ccsd_ctx* c, int k, int l) {
   if (k > nr || l > nr) throw Err(CCSD_ERR_ARG, "state index beyond the solved roots");
   if ((k > 0 || l > 0) && !(c->have_right && c->have_left)) throw Err(CCSD_ERR_STATE, "EOM states not solved");
 }
+
+}  // namespace
+
+extern "C" {
 
 ccsd_status ccsd_transition_density(ccsd_handle c, int k, int l, double* D) {
   return guarded(c, [&] {
@@ -1822,6 +1829,61 @@ ccsd_status ccsd_connection_term(ccsd_handle c, int k, int l, int ndir, const do
       CUDA_OK(cudaMemcpyAsync(O + d, out.p, sizeof(double), cudaMemcpyDefault, c->st));
       sync(c);
     }
+  });
+}
+
+}  // extern "C"
+
+namespace {
+// N_k^L = 1/|<HF|(l0 + L_k) exp(-T)|| (the left state has no component beyond the doubles):
+// a_0 = <psi^L|HF> = l0 - <L|(t1, t2 - t1 t1)>, a_mu = <L|tau_mu (1 - T1)|HF>, and the
+// biorthonormal-bra metric of a
+double left_norm(ccsd_ctx* c, int k) {
+  if (!c->have_ground) throw Err(CCSD_ERR_STATE, "ground state not solved");
+  if (k < 0 || k > (int)c->omega.size()) throw Err(CCSD_ERR_ARG, "state index beyond the solved roots");
+  if (k > 0 && !(c->have_right && c->have_left)) throw Err(CCSD_ERR_STATE, "EOM states not solved");
+  const int64_t dim = c->dim;
+  const double l0 = (k == 0) ? 1.0 : 0.0;
+  const double* L = left_vec(c, k);
+  DevBuf x(dim), r(dim), a(dim), out(1);
+  launch_t2_minus_t1t1(c->vs, c->t.p, x.p, c->st);
+  const double a0 = l0 - gram(c, L, dim, 1, x.p, dim, 1)[0];
+  // R = (-t1, 0): <L|tau (1 + R)|HF> gives a
+  CUDA_OK(cudaMemsetAsync(r.p, 0, dim * sizeof(double), c->st));
+  launch_axpby(c->n1, -1.0, c->t.p, 0.0, r.p, c->st);
+  launch_tau_expectation(c->vs, 1.0, L, r.p, a.p, c->st);
+  launch_bra_metric(c->vs, a.p, out.p, c->ex->scratch(1024), c->st);
+  double q = 0.0;
+  CUDA_OK(cudaMemcpyAsync(&q, out.p, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  sync(c);
+  const double norm2 = a0 * a0 + q;
+  if (!(norm2 > 0.0)) throw Err(CCSD_ERR_NOT_CONVERGED, "left state of zero norm");
+  return 1.0 / std::sqrt(norm2);
+}
+
+}  // namespace
+
+extern "C" {
+
+ccsd_status ccsd_left_norm(ccsd_handle c, int k, double* N) {
+  return guarded(c, [&] {
+    if (!N) throw Err(CCSD_ERR_ARG, "null pointer");
+    *N = left_norm(c, k);
+  });
+}
+
+ccsd_status ccsd_normalized_coupling(ccsd_handle c, int k, int l, int ndir, const double* dh, const double* dB,
+                                     double* F) {
+  return guarded(c, [&] {
+    if (ndir < 1 || !dh || !dB || !F) throw Err(CCSD_ERR_ARG, "bad arguments");
+    check_pair(c, k, l);
+    const double nk = left_norm(c, k), nl = left_norm(c, l);
+    std::vector<double> fkl(ndir), flk(ndir);
+    compute_densities(c, k, l);
+    contract_densities(c, ndir, dh, dB, fkl.data());
+    compute_densities(c, l, k);
+    contract_densities(c, ndir, dh, dB, flk.data());
+    for (int d = 0; d < ndir; ++d) F[d] = 0.5 * (nk / nl * fkl[d] - nl / nk * flk[d]);
   });
 }
 

@@ -775,6 +775,67 @@ __global__ void k_sum_final(int nb, const double* work, double* out) {
   out[0] = s;
 }
 
+// partial sums of the biorthonormal-bra metric of a vector a (singles [i][a], doubles
+// [i][j][a][b] pair-symmetric): 1/2 a_ia^2 and (2 A_ijab^2 + A_ijab A_ijba)/12, plus
+// 3/4 A_iiaa^2 on the diagonal ai = bj
+__global__ void k_bra_metric_partial(VecShape vs, const double* __restrict__ a, double* work) {
+  const int o = vs.o, v = vs.v;
+  const int64_t n1 = vs.n1(), n = vs.dim();
+  double s = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double x = a[k];
+    if (k < n1) {
+      s = fma(0.5 * x, x, s);
+      continue;
+    }
+    const int64_t e = k - n1;
+    const int b = (int)(e % v);
+    int64_t r = e / v;
+    const int aa = (int)(r % v);
+    r /= v;
+    const int j = (int)(r % o), i = (int)(r / o);
+    const double xs = a[n1 + (((int64_t)i * o + j) * v + b) * v + aa];
+    s += (2.0 * x * x + x * xs) * (1.0 / 12.0);
+    if (i == j && aa == b) s += 0.75 * x * x;
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) work[blockIdx.x] = sh[0];
+}
+
+// x2[i][j][a][b] = t2[i][j][a][b] - t1[i][a] t1[j][b] (the doubles of exp(-T)'s coefficients, negated)
+__global__ void k_t2_minus_t1t1(VecShape vs, const double* __restrict__ t, double* __restrict__ x) {
+  const int o = vs.o, v = vs.v;
+  const int64_t n1 = vs.n1(), n2 = vs.dim() - n1;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n2; e += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(e % v);
+    int64_t r = e / v;
+    const int aa = (int)(r % v);
+    r /= v;
+    const int j = (int)(r % o), i = (int)(r / o);
+    x[n1 + e] = t[n1 + e] - t[(int64_t)i * v + aa] * t[(int64_t)j * v + b];
+  }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n1; e += (int64_t)gridDim.x * blockDim.x)
+    x[e] = t[e];
+}
+
+void launch_bra_metric(const VecShape& s, const double* a, double* out, double* work, cudaStream_t st) {
+  const int nb = 512;
+  count_launches(2);
+  k_bra_metric_partial<<<nb, 256, 0, st>>>(s, a, work);
+  k_sum_final<<<1, 32, 0, st>>>(nb, work, out);
+}
+
+void launch_t2_minus_t1t1(const VecShape& s, const double* t, double* x, cudaStream_t st) {
+  count_launches(1);
+  k_t2_minus_t1t1<<<(int)std::min<int64_t>((s.dim() + 255) / 256, 152 * 16), 256, 0, st>>>(s, t, x);
+}
+
 void launch_dot(int64_t n, const double* x, const double* y, double* out, double* work, cudaStream_t st) {
   int nb = 512;
   count_launches(2);

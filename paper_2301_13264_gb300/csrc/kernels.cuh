@@ -81,6 +81,11 @@ void launch_argmaxabs(int64_t n, const double* x, double* out, double* work, cud
 // t-eta first term: <L|tau_sigma|(r0 + R)> for all packed sigma (see capi.cpp).
 void launch_tau_expectation(const VecShape& s, double r0, const double* L, const double* R, double* y,
                             cudaStream_t st);
+// out[0] = the biorthonormal-bra metric of a (1/2 sum a_1^2 + sum (2 A^2 + A A_swap(ab))/12
+// + 3/4 sum over the diagonal ai = bj), two-pass through work (>= 512 doubles).
+void launch_bra_metric(const VecShape& s, const double* a, double* out, double* work, cudaStream_t st);
+// x = (t1, t2 - t1 (x) t1): singles copied, doubles t2[i][j][a][b] - t1[i][a] t1[j][b].
+void launch_t2_minus_t1t1(const VecShape& s, const double* t, double* x, cudaStream_t st);
 // out[p][q] = (D[p][q] - D[q][p]) / 2 for an n x n matrix (out must not overlap D).
 void launch_antisymmetric_part(int n, const double* D, double* out, cudaStream_t st);
 

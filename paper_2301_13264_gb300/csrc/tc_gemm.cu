@@ -363,20 +363,15 @@ __global__ void __launch_bounds__(256) k_split_gather(const double* __restrict__
       }
     }
     __syncthreads();
-    // the split in FP32 from the rounded value: each remainder f - bf16(f) is exact in FP32
-    // (at most 17 and then 10 significant bits), so the slices carry the 24-bit significand
-    // of the value up to the last slice's rounding, as an FP64 split would within 2^-24
+    // split_bf16: integer and FP32 operations only (the FP64 pipe issues 2 per clock per SM)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int rr = ty + 8 * i;
-      float x0 = f64_to_f32_rn(tile[rr][2 * tx]), x1 = f64_to_f32_rn(tile[rr][2 * tx + 1]);
-      __nv_bfloat162* d = reinterpret_cast<__nv_bfloat162*>(dst + (r0 + rr) * Kp + k0 + 2 * tx);
-      for (int s = 0; s < S; ++s) {
-        const __nv_bfloat16 b0 = __float2bfloat16_rn(x0), b1 = __float2bfloat16_rn(x1);
-        d[s * (plane / 2)] = __halves2bfloat162(b0, b1);
-        x0 -= __bfloat162float(b0);
-        x1 -= __bfloat162float(b1);
-      }
+      unsigned short q0[3], q1[3];
+      split_bf16(tile[rr][2 * tx], S, q0);
+      split_bf16(tile[rr][2 * tx + 1], S, q1);
+      unsigned int* d = reinterpret_cast<unsigned int*>(dst + (r0 + rr) * Kp + k0 + 2 * tx);
+      for (int s = 0; s < S; ++s) d[s * (plane / 2)] = (unsigned int)q0[s] | ((unsigned int)q1[s] << 16);
     }
     __syncthreads();
   }

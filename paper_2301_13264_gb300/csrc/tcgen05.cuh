@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -131,27 +132,61 @@ inline int raster_group(int mt, int bn) {
   return mt < g ? mt : g;
 }
 
-// Round-to-nearest-even conversion of a double to float with integer operations only, so
-// that operand packing does not queue on the FP64 pipe (a few lanes per SM on this chip).
-// Values below the float normal range flush to a signed zero; overflow gives infinity;
-// NaN stays NaN.
-__device__ __forceinline__ float f64_to_f32_rn(double x) {
+// S bf16 slices of x (S = 2 or 3), x ~ out[0] + out[1] (+ out[2]), as the FP64 split
+// x_0 = bf16(x), x_1 = bf16(x - x_0), x_2 = bf16(x - x_0 - x_1) computes them, in integer and
+// FP32 operations only: x_0 is rounded (to nearest, ties to even) straight from the double's
+// bits, the remainder x - x_0 is formed exactly as an integer (at most 45 significant bits) and
+// rounded once to float (relative error 2^-24 of the remainder, 2^-32 of x), and the later
+// slices are split from that float, each FP32 remainder being exact.  Values outside the bf16
+// exponent range flush to zero or saturate to infinity; NaN gives NaN.
+__device__ __forceinline__ void split_bf16(double x, int S, unsigned short (&out)[3]) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const unsigned int sign = (unsigned int)(u >> 63) << 31;
-  const int e = (int)((u >> 52) & 0x7FFu);
-  const unsigned long long m = u & ((1ull << 52) - 1);
-  if (e == 0x7FF) return __uint_as_float(sign | 0x7F800000u | (m ? 0x400000u : 0u));
-  int ef = e - 1023 + 127;
-  if (e == 0 || ef <= 0) return __uint_as_float(sign);
-  unsigned long long keep = m >> 29;
-  const unsigned long long rest = m & ((1ull << 29) - 1), half = 1ull << 28;
-  if (rest > half || (rest == half && (keep & 1ull))) ++keep;
-  if (keep == (1ull << 23)) {
-    keep = 0;
-    ++ef;
+  const unsigned int sign16 = (unsigned int)(u >> 63) << 15;
+  const int E = (int)((u >> 52) & 0x7FFu);
+  out[0] = out[1] = out[2] = (unsigned short)sign16;
+  if (E == 0x7FF) {  // Inf or NaN: carried by the first slice
+    out[0] = (unsigned short)(sign16 | 0x7F80u | ((u & ((1ull << 52) - 1)) ? 0x40u : 0u));
+    return;
   }
-  if (ef >= 255) return __uint_as_float(sign | 0x7F800000u);
-  return __uint_as_float(sign | ((unsigned int)ef << 23) | (unsigned int)keep);
+  const int ef = E - 1023 + 127;
+  if (E == 0 || ef <= 0) return;  // below the bf16 normal range
+  const unsigned long long M = (u & ((1ull << 52) - 1)) | (1ull << 52);  // 53-bit significand
+  unsigned long long q = M >> 45;                                          // 8 bits
+  const unsigned long long rest = M & ((1ull << 45) - 1), half = 1ull << 44;
+  if (rest > half || (rest == half && (q & 1ull))) ++q;
+  const long long d = (long long)M - (long long)(q << 45);  // x - x_0 = +-d 2^(E - 1075), |d| <= 2^44
+  const int e0 = (q == 256ull) ? ef + 1 : ef;
+  if (e0 >= 255) {
+    out[0] = (unsigned short)(sign16 | 0x7F80u);
+    return;
+  }
+  out[0] = (unsigned short)(sign16 | ((unsigned int)e0 << 7) | (unsigned int)(q == 256ull ? 0 : (q & 0x7Fu)));
+  if (d == 0) return;
+  // the remainder as a float: |d| rounded to 24 significant bits, exponent from its top bit
+  const unsigned long long a = (unsigned long long)(d < 0 ? -d : d);
+  const int p = 63 - __clzll((long long)a);  // a in [2^p, 2^(p+1)), p <= 44
+  unsigned long long mant;
+  int fe = p + (E - 1075) + 127;
+  if (p > 23) {
+    const int drop = p - 23;
+    mant = a >> drop;
+    const unsigned long long r2 = a & ((1ull << drop) - 1), h2 = 1ull << (drop - 1);
+    if (r2 > h2 || (r2 == h2 && (mant & 1ull))) ++mant;
+    if (mant == (1ull << 24)) {
+      mant >>= 1;
+      ++fe;
+    }
+  } else {
+    mant = a << (23 - p);
+  }
+  if (fe <= 0) return;  // the remainder is below the float normal range
+  const unsigned int rsign = ((unsigned int)(u >> 63) ^ (d < 0 ? 1u : 0u)) << 31;
+  float r = __uint_as_float(rsign | ((unsigned int)fe << 23) | (unsigned int)(mant & ((1ull << 23) - 1)));
+  for (int s = 1; s < S; ++s) {
+    const __nv_bfloat16 b = __float2bfloat16_rn(r);
+    out[s] = __bfloat16_as_ushort(b);
+    r -= __bfloat162float(b);
+  }
 }
 
 // 3-D TMA map over bf16 slices [S][rows][Kp]: boxes of 64 K x box_rows rows x 1 slice,
