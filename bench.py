@@ -410,7 +410,7 @@ def run_ours(args, rank, world, local_rank):
            "config": {"workload": f"{args.workload} o={o} v={v} naux={naux}", "nvec": args.nvec,
                       "step": f"right + left block transform of {args.nvec} vectors",
                       "precision": args.precision, "splits": args.splits,
-                      "l2": "inputs larger than L2 (vvvv integrals 21.6 GB)"},
+                      "l2": f"inputs larger than L2 (vvvv integrals {v ** 4 * 8 / 1e9:.1f} GB)"},
            "right_transforms_per_s": right_rate, "left_transforms_per_s": left_rate,
            "block1_transforms_per_s": {"right": right_rate1, "left": left_rate1},
            "alg_tflops_per_transform": f_alg / 1e12,

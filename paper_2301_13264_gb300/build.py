@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libccsd_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["ir.cpp", "programs.cpp", "small_linalg.cpp", "capi.cpp", "exec.cu", "kernels.cu", "tc_gemm.cu", "fp64_tc.cu",
-           "ladder.cu", "noalloc.cu", "mlp.cu", "orbital.cpp", "alloc.cpp"]
+           "ladder.cu", "noalloc.cu", "mlp.cu", "orbital.cpp", "alloc.cpp", "subspace.cu"]
 
 
 def nvcc() -> str:

@@ -26,6 +26,7 @@
 #include "orbital.h"
 #include "programs.h"
 #include "small_linalg.h"
+#include "subspace.h"
 
 static_assert(ccsd::mlp::kParams == CCSD_MLP_PARAMS, "model size");
 
@@ -409,7 +410,11 @@ class Davidson {
         X(nroots * c->dim),
         AX(nroots * c->dim),
         Rz(nroots * c->dim),
-        Gm(maxsub_ * maxsub_, 0.0) {
+        Gd(maxsub_ * maxsub_),
+        Sout(2 * nroots + maxsub_ * nroots + 1),
+        Swork((subspace_work_bytes(maxsub_) + 7) / 8),
+        Tg(nroots) {
+    CUDA_OK(cudaMemsetAsync(Gd.p, 0, (size_t)maxsub_ * maxsub_ * sizeof(double), c->st));
     const int64_t dim = dim_;
     // guesses: the given vectors, else singles unit vectors of the lowest orbital-energy differences
     if (init && (int)init->size() >= nroots) {
@@ -452,78 +457,45 @@ class Davidson {
     ccsd_ctx* c = c_;
     const int64_t dim = dim_;
     ++iterations;
-    // extend the projected matrix with the pending block
+    // extend the projected matrix G[i][j] = <V_i|A V_j> (on the device) with the pending block
     {
-      std::vector<double> a = gram(c, V.p, dim, first + count, AV.p + first * dim, dim, count);
-      std::vector<double> b = gram(c, V.p + first * dim, dim, count, AV.p, dim, first);
-      for (int i = 0; i < first + count; ++i)
-        for (int j = 0; j < count; ++j) Gm[i * maxsub_ + first + j] = a[i * count + j];
-      for (int i = 0; i < count; ++i)
-        for (int j = 0; j < first; ++j) Gm[(first + i) * maxsub_ + j] = b[i * first + j];
+      double* work = c->ex->scratch(wdot_work_size(first + count, std::max(count, first)));
+      launch_wdot(c->vs, V.p, dim, first + count, AV.p + first * dim, dim, count, Gd.p + first, maxsub_, work, c->st);
+      if (first > 0)
+        launch_wdot(c->vs, V.p + first * dim, dim, count, AV.p, dim, first, Gd.p + (int64_t)first * maxsub_, maxsub_,
+                    work, c->st);
     }
     m_ = first + count;
     count = 0;
     const int m = m_, nroots = nroots_;
-    std::vector<double> G(m * m);
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) G[i * m + j] = Gm[i * maxsub_ + j];
-    std::vector<std::complex<double>> all = eigenvalues(m, G);
-    std::sort(all.begin(), all.end(), [](auto& a, auto& b) { return a.real() < b.real(); });
-    if ((int)all.size() < nroots) throw Err(CCSD_ERR_NOT_CONVERGED, "subspace too small");
+    if (m < nroots) throw Err(CCSD_ERR_NOT_CONVERGED, "subspace too small");
+    // the subspace eigenproblem in FP64 on the GPU: Ritz values (the lowest, or the ones nearest
+    // the targets) and their coefficient vectors U[m][nroots] (subspace.cu).  A complex pair
+    // a +- ib among the wanted values is usually transient (a small subspace of a non-symmetric
+    // matrix); the pair's real 2-D invariant subspace is then spanned by u (inverse iteration
+    // at a) and (G - a)u, which serve as the two Ritz-like vectors with shift a.  A pair that
+    // survives many expansions is reported.
+    const bool tgt = (int)targets.size() == nroots;
+    if (tgt)
+      CUDA_OK(cudaMemcpyAsync(Tg.p, targets.data(), nroots * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    launch_subspace_step(m, Gd.p, maxsub_, nroots, tgt ? Tg.p : nullptr, Sout.p, Swork.p, c->st);
+    std::vector<double> head(2 * nroots);
     double scale = 0.0;
-    for (auto& e : all) scale = std::max(scale, std::abs(e));
-    // wanted roots: the lowest by real part, or the ones nearest the given targets
-    std::vector<std::complex<double>> ev(all.begin(), all.begin() + nroots);
-    if ((int)targets.size() == nroots) {
-      std::vector<char> used(all.size(), 0);
-      for (int k = 0; k < nroots; ++k) {
-        int best = -1;
-        for (int q = 0; q < (int)all.size(); ++q)
-          if (!used[q] && (best < 0 || std::fabs(all[q].real() - targets[k]) < std::fabs(all[best].real() - targets[k])))
-            best = q;
-        used[best] = 1;
-        ev[k] = all[best];
-      }
-    }
-    // A complex pair a +- ib among the wanted subspace eigenvalues is usually
-    // transient (a small subspace of a non-symmetric matrix); the pair's real 2-D
-    // invariant subspace is then spanned by u (inverse iteration at a) and (G - a)u,
-    // which serve as the two Ritz-like vectors with shift a.  A pair that survives
-    // many expansions is reported.
+    CUDA_OK(cudaMemcpyAsync(head.data(), Sout.p, 2 * nroots * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CUDA_OK(cudaMemcpyAsync(&scale, Sout.p + 2 * nroots + (int64_t)m * nroots, sizeof(double), cudaMemcpyDeviceToHost,
+                            c->st));
+    sync(c);
     bool cplx = false;
-    for (int k = 0; k < nroots; ++k) cplx |= std::fabs(ev[k].imag()) > 1e-9 * std::max(scale, 1.0);
+    omega.assign(nroots, 0.0);
+    for (int k = 0; k < nroots; ++k) {
+      omega[k] = head[k];
+      cplx |= std::fabs(head[nroots + k]) > 1e-9 * std::max(scale, 1.0);
+    }
     complex_run_ = cplx ? complex_run_ + 1 : 0;
     if (complex_run_ > 12) throw Err(CCSD_ERR_COMPLEX_ROOT, "complex eigenvalue among the wanted roots");
-    std::vector<double> U(m * nroots);
-    omega.assign(nroots, 0.0);
-    std::vector<double> prev;
-    for (int k = 0; k < nroots; ++k) {
-      omega[k] = ev[k].real();
-      const bool is_c = std::fabs(ev[k].imag()) > 1e-9 * std::max(scale, 1.0);
-      const bool partner = is_c && k > 0 && !prev.empty() && std::fabs(ev[k].real() - ev[k - 1].real()) <=
-                                                                 1e-12 * std::max(scale, 1.0);
-      std::vector<double> u(m);
-      if (partner) {  // (G - a) u_prev, normalised
-        double nn = 0.0;
-        for (int i = 0; i < m; ++i) {
-          double s = -omega[k] * prev[i];
-          for (int j = 0; j < m; ++j) s += G[i * m + j] * prev[j];
-          u[i] = s;
-          nn += s * s;
-        }
-        for (int i = 0; i < m; ++i) u[i] /= std::sqrt(std::max(nn, 1e-300));
-        prev.clear();
-      } else {
-        u = eigenvector(m, G, omega[k]);
-        if (is_c)
-          prev = u;
-        else
-          prev.clear();
-      }
-      for (int i = 0; i < m; ++i) U[i * nroots + k] = u[i];
-    }
-    lincomb(c, V.p, dim, m, U, X.p, dim, nroots, false);
-    lincomb(c, AV.p, dim, m, U, AX.p, dim, nroots, false);
+    const double* U = Sout.p + 2 * nroots;
+    launch_lincomb(c->vs, V.p, dim, m, U, nroots, X.p, dim, nroots, false, c->st);
+    launch_lincomb(c->vs, AV.p, dim, m, U, nroots, AX.p, dim, nroots, false, c->st);
     // residuals r_k = A x_k - omega_k x_k (x_k has unit norm up to roundoff)
     std::vector<double> xn = gram(c, X.p, dim, nroots, X.p, dim, nroots);
     std::vector<int> todo;
@@ -542,7 +514,7 @@ class Davidson {
     int base = m_;
     if (m_ + (int)todo.size() > maxsub_) {  // restart from the current Ritz vectors
       CUDA_OK(cudaMemcpyAsync(V.p, X.p, nroots * dim * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
-      std::fill(Gm.begin(), Gm.end(), 0.0);
+      CUDA_OK(cudaMemsetAsync(Gd.p, 0, (size_t)maxsub_ * maxsub_ * sizeof(double), c->st));
       base = 0;
       m_ = 0;
       for (size_t q = 0; q < todo.size(); ++q)
@@ -604,7 +576,10 @@ class Davidson {
   int64_t dim_;
   int maxsub_;
   DevBuf V, AV, X, AX, Rz;
-  std::vector<double> Gm;  // Gm[i][j] = <V_i | A V_j>
+  DevBuf Gd;     // G[i][j] = <V_i | A V_j>, maxsub x maxsub (device)
+  DevBuf Sout;   // subspace step output: Ritz values, imaginary parts, U[m][nroots], scale
+  DevBuf Swork;  // subspace step scratch
+  DevBuf Tg;     // targets (device copy)
   int m_ = 0;
   int complex_run_ = 0;
 };
@@ -855,8 +830,18 @@ void finish_left(ccsd_ctx* c, const std::vector<double>& w, const std::vector<st
   std::vector<double> M(nroots * nroots);
   for (int k = 0; k < nroots; ++k)
     for (int l = 0; l < nroots; ++l) M[k * nroots + l] = gram(c, Lr[k]->p, c->dim, 1, c->R[l]->p, c->dim, 1)[0];
-  std::vector<double> Minv;
-  if (!invert(nroots, M, Minv)) throw Err(CCSD_ERR_DEGENERATE, "left/right overlap matrix is singular");
+  // the inverse in FP64 on the GPU (subspace.cu)
+  std::vector<double> Minv(nroots * nroots);
+  {
+    DevBuf Md(nroots * nroots), Mi(nroots * nroots), wk((small_inverse_work_bytes(nroots) + 7) / 8), fl(1);
+    int flag = 0;
+    CUDA_OK(cudaMemcpyAsync(Md.p, M.data(), nroots * nroots * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    launch_small_inverse(nroots, Md.p, Mi.p, (int*)fl.p, wk.p, c->st);
+    CUDA_OK(cudaMemcpyAsync(Minv.data(), Mi.p, nroots * nroots * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CUDA_OK(cudaMemcpyAsync(&flag, fl.p, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    sync(c);
+    if (flag) throw Err(CCSD_ERR_DEGENERATE, "left/right overlap matrix is singular");
+  }
   c->L.clear();
   for (int k = 0; k < nroots; ++k) {
     c->L.emplace_back(new DevBuf(c->dim));

@@ -274,13 +274,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (lane == 0) mbar_arrive1(acce0 + 8 * b);
         }
         if (ready && row < p.M && !*err) {
+          // read-modify-write of 32 distinct outputs: every load is issued before the first
+          // store, so that they are in flight together (the compiler cannot know that the
+          // strided destinations do not alias and would otherwise serialise them)
+          const bool acc = !(split || p.beta_zero);
+          double old[32];
+          if (acc) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int n = n0 + c + j;
+              old[j] = (n < p.N) ? crow[ostr ? coloff[c + j] : (long long)n * cs] : 0.0;
+            }
+          }
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const int n = n0 + c + j;
             if (n < p.N) {
-              double* dst = crow + (ostr ? coloff[c + j] : (long long)n * cs);
               const double v = empty ? 0.0 : p.alpha * (double)__uint_as_float(r[j]);
-              *dst = (split || p.beta_zero) ? v : (*dst + v);
+              crow[ostr ? coloff[c + j] : (long long)n * cs] = acc ? old[j] + v : v;
             }
           }
         }
