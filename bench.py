@@ -28,11 +28,10 @@ import numpy as np  # noqa: E402
 
 METRIC = "Jacobian transforms/s and time-to-converged coupling at o=33,v=228 vs FP64 GPU form"
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
-# DRAM bytes (read + write) of one ladder contraction (its + and - GEMM launches) from
-# an ncu capture of this benchmark (profiles/k_tc_gemm_ladder_thymine_adz.md), keyed by
-# (workload, nvec, products); None (unknown) for other settings
-LADDER_TRAFFIC = {("thymine_adz", 8, 6): (86.01 + 0.939 + 93.10 + 0.938) * 1e9,
-                  ("thymine_dz", 8, 6): (3.93 + 0.2726 + 3.93 + 0.2725) * 1e9}
+# DRAM bytes (read + write) of one ladder contraction (its + and - GEMM launches) from an
+# ncu capture of the current kernel, keyed by (workload, nvec, products); a missing entry
+# reports null (the counters are retaken whenever the kernel changes)
+LADDER_TRAFFIC = {}
 UNIT = "transforms/s"
 
 
