@@ -137,7 +137,8 @@ ccsd_status eom_solve_left(ccsd_handle h, int nroots, double* omega, int* iters)
 
 /* One block Jacobian transformation at the converged amplitudes:
  * side 0: y_i = A x_i; side 1: y_i = (x_i^T A)^T (Eq. for A), for i < nvec.
- * x, y: [nvec][dim] (host or device). */
+ * x, y: [nvec][dim] (host or device).  Host vectors pass through device staging
+ * buffers that the handle keeps (grown to the largest block seen) until ccsd_destroy. */
 ccsd_status ccsd_jacobian_transform(ccsd_handle h, int side, int nvec, const double* x, double* y);
 
 /* Residual Omega(t) and energy at amplitudes t[dim] (no convergence implied).

@@ -103,6 +103,9 @@ struct ccsd_ctx {
   // densities of the last pair
   int dens_k = -1, dens_l = -1;
   DevBuf Dd, Zd;
+  // device staging of host-memory trial vectors for ccsd_jacobian_transform, kept between calls
+  // (grown as needed) so that a host-pointer call allocates and frees nothing in steady state
+  DevBuf stage_x, stage_y;
   long long prof_launch0 = 0;
   DevBuf guess_model;  // MLP model (floats) for the starting doubles, or empty
   DevBuf mult_model;   // MLP model for the starting doubles of the multiplier solves, or empty
@@ -1662,17 +1665,17 @@ ccsd_status ccsd_jacobian_transform(ccsd_handle c, int side, int nvec, const dou
   return guarded(c, [&] {
     if ((side != 0 && side != 1) || nvec < 1 || !x || !y) throw Err(CCSD_ERR_ARG, "bad arguments");
     const int64_t dim = c->dim;
-    DevBuf xd, yd;
     const double* xp = x;
     double* yp = y;
     bool xdev = is_device_ptr(x), ydev = is_device_ptr(y);
     if (!xdev) {
-      to_device(c, x, nvec * dim, xd);
-      xp = xd.p;
+      if (c->stage_x.n < nvec * dim) c->stage_x.alloc(nvec * dim);
+      CUDA_OK(cudaMemcpyAsync(c->stage_x.p, x, nvec * dim * sizeof(double), cudaMemcpyDefault, c->st));
+      xp = c->stage_x.p;
     }
     if (!ydev) {
-      yd.alloc(nvec * dim);
-      yp = yd.p;
+      if (c->stage_y.n < nvec * dim) c->stage_y.alloc(nvec * dim);
+      yp = c->stage_y.p;
     }
     const int block = 16;
     for (int s = 0; s < nvec; s += block) {
