@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--guess-train", type=int, default=40, help="--guess-eval: number of training systems")
     ap.add_argument("--guess-scale", type=float, default=4.0, help="--guess-eval: size reduction of the training systems")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-coupling comparison of the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -418,6 +419,15 @@ def run_ours(args, rank, world, local_rank):
            "roofline": roofline, "e2e": e2e, "gpu_launches": prof["launches"], "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_entry(args.workload)
+    if rank == 0 and world == 1 and not args.no_ttc:
+        # time to converged coupling at equal accuracy, measured in this run: the refined mixed
+        # form against the FP64-grade tensor-core form (FP64-accurate; the DFMA form takes minutes)
+        # at the thymine/cc-pVDZ size, where both finish in about a minute and a half
+        t = measure_ttc("thymine_dz", ["mixed", "fp64tc"], args.splits, 1e-9, 96)
+        m = t["forms"]["mixed"]
+        out["ttc"] = {"workload": t["workload"], "pairs": t["pairs"], "thresholds": t["thresholds"],
+                      "mixed_s": m["seconds"], "reference_form": "fp64tc (FP64-grade tensor-core products)",
+                      "reference_s": t["forms"]["fp64tc"]["seconds"], **m["vs_fp64tc"]}
     B.ccsd_destroy(h)
     if rank == 0:
         print(json.dumps(out), flush=True)
@@ -439,22 +449,27 @@ def run_ttc(args):
     the same convergence thresholds (1e-10 residual, --tol-eom (1e-8) EOM, 1e-9
     linear).  Every form is compared, root by root, with the FP64 DFMA form when
     it ran, else with the FP64-grade tensor-core form."""
+    forms = ["mixed", "fp64"] if args.ttc == "both" else args.ttc.split(",")
+    print(json.dumps(measure_ttc(args.workload, forms, args.splits, args.tol_eom, args.max_sub)), flush=True)
+
+
+def measure_ttc(workload_name, forms, splits, tol_eom, max_sub):
+    """The time-to-converged-coupling comparison of run_ttc as a dict."""
     import torch
     from paper_2301_13264_gb300 import binding as B
     from paper_2301_13264_gb300.synth import workload
 
-    H = workload(args.workload)
-    forms = ["mixed", "fp64"] if args.ttc == "both" else args.ttc.split(",")
+    H = workload(workload_name)
     for f in forms:
         if f not in ("mixed", "fp64", "fp64tc"):
             raise SystemExit(f"unknown form {f!r}")
     out = {"metric": "time-to-converged coupling", "unit": "s", "higher_is_better": False,
-           "workload": f"{args.workload} o={H.o} v={H.v} naux={H.naux}", "pairs": [[1, 2], [0, 1], [2, 0]],
+           "workload": f"{workload_name} o={H.o} v={H.v} naux={H.naux}", "pairs": [[1, 2], [0, 1], [2, 0]],
            "forms": {}}
     for form in forms:
         prec = precision_of(form)
-        opt = B.ccsd_default_options(precision=prec, splits=args.splits, tol_res=1e-10, tol_eom=args.tol_eom,
-                                     tol_lin=1e-9, max_iter=300, refine=1, davidson_max_sub=args.max_sub)
+        opt = B.ccsd_default_options(precision=prec, splits=splits, tol_res=1e-10, tol_eom=tol_eom,
+                                     tol_lin=1e-9, max_iter=300, refine=1, davidson_max_sub=max_sub)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = B.ccsd_create(H.eps, H.h, H.B, H.o, H.v, H.naux, opt)
@@ -473,7 +488,7 @@ def run_ttc(args):
                               "e_ccsd": e, "omega": w, "F": F, "iters": [it_g, it_r, it_l],
                               "stats": B.ccsd_stats(h)}
         B.ccsd_destroy(h)
-    out["thresholds"] = {"tol_res": 1e-10, "tol_eom": args.tol_eom, "tol_lin": 1e-9, "davidson_max_sub": args.max_sub}
+    out["thresholds"] = {"tol_res": 1e-10, "tol_eom": tol_eom, "tol_lin": 1e-9, "davidson_max_sub": max_sub}
     ref_name = "fp64" if "fp64" in out["forms"] else ("fp64tc" if "fp64tc" in out["forms"] else None)
     if ref_name:
         f = out["forms"][ref_name]
@@ -487,7 +502,7 @@ def run_ttc(args):
                 "coupling_rel_diff_per_pair": [abs(a - b) / abs(b) for a, b in zip(m["F"], f["F"])],
                 "omega_diff": max(abs(a - b) for a, b in zip(m["omega"], f["omega"])),
                 "coupling_rel_diff": max(abs(a - b) / abs(b) for a, b in zip(m["F"], f["F"]))}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def batch_shapes(nsys, seed=4):

@@ -53,6 +53,10 @@ def test_transform_benchmark_json(monkeypatch, capsys):
     monkeypatch.setattr(B, "ccsd_profile_start", lambda h: None)
     monkeypatch.setattr(B, "ccsd_profile_stop", lambda h: {k: 1.0 for k, _ in B.ProfileData._fields_})
     monkeypatch.setattr(B, "ccsd_destroy", lambda h: None)
+    monkeypatch.setattr(B, "eom_solve_right", lambda h, n: ([0.3, 0.4], 5))
+    monkeypatch.setattr(B, "eom_solve_left", lambda h, n: ([0.3, 0.4], 6))
+    monkeypatch.setattr(B, "ccsd_derivative_coupling", lambda h, k, l, nd, dh, dB: [0.01 * (k + 2 * l)])
+    monkeypatch.setattr(B, "ccsd_stats", lambda h: {"flops_fp64": 1.0, "flops_tc": 2.0, "gemms": 3, "tc_gemms": 4})
     monkeypatch.setattr(synth, "workload", lambda name: synth.make_hamiltonian(2, 4, 6, seed=0))
     monkeypatch.setattr(sys, "argv", ["bench.py", "--no-e2e", "--no-cpu-baseline", "--steps", "2", "--warmup", "3",
                                       "--nvec", "3"])
@@ -68,6 +72,10 @@ def test_transform_benchmark_json(monkeypatch, capsys):
     assert out["steps"] == 2 and out["warmup"] == 3 and out["n_gpus"] == 1
     for key in ("bound", "achieved", "peak", "unit", "frac", "traffic", "frac_of_fp64_peak"):
         assert key in out["roofline"], key
+    # the time-to-coupling comparison measured in the same run
+    for key in ("workload", "mixed_s", "reference_s", "reference_form", "speedup", "energy_diff",
+                "omega_diff_per_root", "coupling_rel_diff_per_pair"):
+        assert key in out["ttc"], key
     # warm-up and timed steps (3 + 2 steps of right + left at nvec), the two separate 8-vector runs per
     # side, then one untimed and two timed single-vector transforms per side
     assert calls[:10] == [(0, 3), (1, 3)] * 5
