@@ -62,6 +62,8 @@ def parse():
                     help="instead, train the learned starts on smaller systems and compare iterations at the workload")
     ap.add_argument("--guess-train", type=int, default=40, help="--guess-eval: number of training systems")
     ap.add_argument("--guess-scale", type=float, default=4.0, help="--guess-eval: size reduction of the training systems")
+    ap.add_argument("--contractions", default=None,
+                    help="write a per-contraction table (markdown) of the timed steps to this file")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-coupling comparison of the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -100,6 +102,41 @@ def load_peaks():
 # a <= b, c <= d) form: o^2 v^4 / 4 multiply-adds per vector, a quarter of its
 # label product
 # ---------------------------------------------------------------------------
+ENGINES = {0: "FP64 DFMA", 1: "split-bf16 TC", 2: "FP64-grade TC"}
+
+
+def contraction_table(records, steps: int, title: str) -> str:
+    """Markdown table of the GEMM launches of `steps` benchmark steps, one row per contraction
+    (its launches summed over the steps and divided by them), slowest first."""
+    rows = {}
+    n_tc = 0  # position among the tensor-core GEMM launches (an ncu launch-skip count)
+    for r in records:
+        key = (r["label"], r["engine"], r["batch"], r["m"], r["n"], r["k"])
+        e = rows.setdefault(key, {"launches": 0, "ms": 0.0, "flops": 0.0, "issued": 0.0, "ladder": r["ladder"],
+                                  "first": n_tc if r["engine"] != 0 else None})
+        n_tc += r["engine"] != 0
+        e["launches"] += 1
+        e["ms"] += r["ms"]
+        e["flops"] += r["flops"]
+        e["issued"] += r["issued_flops"]
+    total = sum(e["ms"] for e in rows.values()) / steps
+    lines = [f"Per-contraction GEMM time of one benchmark step: {title}", "",
+             f"{len(records) // max(steps, 1)} GEMM launches, {total:.1f} ms per step (CUDA events around each "
+             "contraction on the library's stream; operand slicing included for the tensor-core forms).", "",
+             "| contraction | engine | batch × M × N × K | launches | ms | share | alg. TFLOP/s | issued TFLOP/s "
+             "| first TC launch |",
+             "|---|---|---|---:|---:|---:|---:|---:|---:|"]
+    for (label, eng, b, m, n, k), e in sorted(rows.items(), key=lambda kv: -kv[1]["ms"]):
+        ms = e["ms"] / steps
+        sec = max(e["ms"], 1e-9) * 1e-3
+        shape = (f"{b} × " if b > 1 else "") + f"{m} × {n} × {k}"
+        lines.append(f"| `{label}` | {ENGINES.get(eng, eng)}{' (ladder)' if e['ladder'] else ''} | {shape} | "
+                     f"{e['launches'] / steps:g} | {ms:.2f} | {ms / max(total, 1e-9):.1%} | "
+                     f"{e['flops'] / sec / 1e12:.1f} | {e['issued'] / sec / 1e12:.1f} | "
+                     f"{'—' if e['first'] is None else e['first']} |")
+    return "\n".join(lines) + "\n"
+
+
 def transform_flops(o, v, naux, which="jvp"):
     """(all contractions, the ladder's share) in flops for one vector."""
     from paper_2301_13264_gb300 import binding as B
@@ -319,6 +356,11 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.nvtx.range_pop()
     prof = B.ccsd_profile_stop(h)
     clk = clocks.stop()
+    if args.contractions and rank == 0:
+        with open(args.contractions, "w") as f:
+            f.write(contraction_table(B.ccsd_profile_records(h), args.steps,
+                                      f"{args.workload} o={o} v={v} naux={naux}, {args.nvec}-vector blocks, "
+                                      f"{args.precision} (S = {args.splits})"))
     ms = ev0.elapsed_time(ev1)
     ms = allreduce_max(ms, world, "cuda")
     value = job_throughput(2 * args.nvec * args.steps, world, ms / 1e3)

@@ -410,6 +410,26 @@ typedef struct {
 ccsd_status ccsd_profile_start(ccsd_handle h);
 ccsd_status ccsd_profile_stop(ccsd_handle h, ccsd_profile_data* out);
 
+/* One GEMM launch of the last profile (between ccsd_profile_start and ccsd_profile_stop),
+ * in launch order: the contraction of the library's tensor program it ran, the arithmetic
+ * form, the GEMM shape (batch x M x N x K after the contraction's labels are grouped), the
+ * device time from the CUDA events around it (operand slicing included for the tensor-core
+ * forms), the algorithmic flops 2 batch M N K and the flops issued (split products and
+ * padding included).  The particle-particle ladder runs as two pair-packed GEMMs (+ and -
+ * pair combinations, Mp x v(v+1)/2 x v(v+1)/2), each a record with ladder = 1. */
+typedef struct {
+  char label[160];            /* out[labels] += a[labels] * b[labels], truncated, NUL-terminated */
+  int engine;                 /* CCSD_GEMM_FP64, CCSD_GEMM_SPLIT or CCSD_GEMM_FP64_TC */
+  int ladder;
+  long long batch, m, n, k;
+  double ms, flops, issued_flops;
+} ccsd_profile_record;
+
+/* Copies min(max, count) records of the last ccsd_profile_stop into out (host memory; out
+ * may be NULL when max is 0) and sets *count to the number there are.  Errors: CCSD_ERR_ARG
+ * (count NULL, max < 0, out NULL with max > 0). */
+ccsd_status ccsd_profile_records(ccsd_handle h, ccsd_profile_record* out, int max, int* count);
+
 const char* ccsd_strerror(ccsd_status s);
 const char* ccsd_last_error(ccsd_handle h);
 void ccsd_destroy(ccsd_handle h);

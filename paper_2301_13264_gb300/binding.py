@@ -110,6 +110,8 @@ def lib():
         L.ccsd_profile_start.restype = ctypes.c_int
         L.ccsd_profile_stop.argtypes = [_P, ctypes.POINTER(ProfileData)]
         L.ccsd_profile_stop.restype = ctypes.c_int
+        L.ccsd_profile_records.argtypes = [_P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.ccsd_profile_records.restype = ctypes.c_int
         L.ccsd_strerror.argtypes = [ctypes.c_int]
         L.ccsd_strerror.restype = ctypes.c_char_p
         L.ccsd_last_error.argtypes = [_P]
@@ -328,6 +330,27 @@ def ccsd_profile_stop(h) -> dict:
     d = ProfileData()
     _check(h, lib().ccsd_profile_stop(h, ctypes.byref(d)))
     return {name: getattr(d, name) for name, _ in ProfileData._fields_}
+
+
+class ProfileRecord(ctypes.Structure):
+    _fields_ = [("label", ctypes.c_char * 160), ("engine", ctypes.c_int), ("ladder", ctypes.c_int),
+                ("batch", ctypes.c_longlong), ("m", ctypes.c_longlong), ("n", ctypes.c_longlong),
+                ("k", ctypes.c_longlong), ("ms", ctypes.c_double), ("flops", ctypes.c_double),
+                ("issued_flops", ctypes.c_double)]
+
+
+def ccsd_profile_records(h) -> list:
+    """The GEMM launches of the last ccsd_profile_stop, in launch order, as dicts."""
+    n = ctypes.c_int(0)
+    _check(h, lib().ccsd_profile_records(h, None, 0, ctypes.byref(n)))
+    recs = (ProfileRecord * max(n.value, 1))()
+    _check(h, lib().ccsd_profile_records(h, recs, n.value, ctypes.byref(n)))
+    out = []
+    for r in recs[: n.value]:
+        d = {name: getattr(r, name) for name, _ in ProfileRecord._fields_}
+        d["label"] = r.label.decode()
+        out.append(d)
+    return out
 
 
 def ccsd_destroy(h):

@@ -2214,6 +2214,30 @@ ccsd_status ccsd_profile_stop(ccsd_handle c, ccsd_profile_data* out) {
   });
 }
 
+ccsd_status ccsd_profile_records(ccsd_handle c, ccsd_profile_record* out, int max, int* count) {
+  return guarded(c, [&] {
+    if (!count || max < 0 || (max > 0 && !out)) throw Err(CCSD_ERR_ARG, "profile records: count, max or out");
+    const auto& lines = c->ex->profile_lines();
+    *count = (int)lines.size();
+    const int n = std::min<int>(max, (int)lines.size());
+    for (int i = 0; i < n; ++i) {
+      const auto& l = lines[i];
+      ccsd_profile_record& r = out[i];
+      std::memset(&r, 0, sizeof(r));
+      std::snprintf(r.label, sizeof(r.label), "%s", l.label.c_str());
+      r.engine = l.engine;
+      r.ladder = l.ladder ? 1 : 0;
+      r.batch = l.batch;
+      r.m = l.m;
+      r.n = l.n;
+      r.k = l.k;
+      r.ms = l.ms;
+      r.flops = l.flops;
+      r.issued_flops = l.issued;
+    }
+  });
+}
+
 long long ccsd_describe_program(const char* which, char* buf, size_t len) {
   try {
     Programs P;

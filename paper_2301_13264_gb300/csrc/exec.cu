@@ -308,6 +308,12 @@ void Executor::exec_contract(const Op& op) {
       CK(cudaEventCreate(&rec.b));
       CK(cudaEventRecord(rec.a, st_));
       rec.flops = flops;
+      rec.engine = prec_ == PREC_FP64_TC ? 2 : 1;
+      rec.batch = Bt;
+      rec.m = M;
+      rec.n = N;
+      rec.k = K;
+      rec.label = op_label(op);
     }
     bool ok = tc_contract((int)M, (int)N, (int)K, A.base, ag, B.base, bg, O.base, cdirect ? sCm : 0,
                           cdirect ? sCn : 0, op.alpha, 1.0, a_const, b_const, cdirect ? nullptr : &om,
@@ -398,6 +404,12 @@ void Executor::exec_contract(const Op& op) {
     CK(cudaEventCreate(&rec.b));
     CK(cudaEventRecord(rec.a, st_));
     rec.flops = flops;
+    rec.engine = 0;
+    rec.batch = Bt;
+    rec.m = M;
+    rec.n = N;
+    rec.k = K;
+    rec.label = op_label(op);
   }
   GemmArgs ga;
   ga.batch = (int)Bt;
@@ -438,14 +450,23 @@ void Executor::profile(bool on) {
   profiling_ = on;
 }
 
+std::string Executor::op_label(const Op& op) const {
+  std::string s = g_.T[op.out.t].name + "[" + op.lo + "] += " + g_.T[op.a.t].name + "[" + op.la + "]";
+  if (op.kind == 'C') s += " * " + g_.T[op.b.t].name + "[" + op.lb + "]";
+  return s;
+}
+
 Executor::ProfTotals Executor::collect() {
   ProfTotals t;
   CK(cudaStreamSynchronize(st_));
   double top = 0.0;
   for (const ProfRec& r : prof_) if (r.tc) top = std::max(top, r.flops);
+  prof_lines_.clear();
+  prof_lines_.reserve(prof_.size());
   for (const ProfRec& r : prof_) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    prof_lines_.push_back(ProfLine{r.label, r.engine, r.ladder, r.batch, r.m, r.n, r.k, (double)ms, r.flops, r.issued});
     if (r.ladder) {
       t.ladder_launches++;
       t.ladder_ms += ms;

@@ -119,7 +119,12 @@ class Executor {
     double flops, issued;
     bool tc;
     bool ladder = false;
+    int engine = 0;  // 0 FP64 DFMA, 1 split-bf16 tensor cores, 2 FP64-grade tensor cores
+    int64_t batch = 1, m = 0, n = 0, k = 0;
+    std::string label;
   };
+  // the contraction an op performs, as out[labels] += a[labels] * b[labels]
+  std::string op_label(const Op& op) const;
   bool profiling_ = false;
   std::vector<ProfRec> prof_;
 
@@ -195,6 +200,16 @@ class Executor {
   };
   void profile(bool on);
   ProfTotals collect();
+  // one line per GEMM launch of the last collect(), in launch order
+  struct ProfLine {
+    std::string label;
+    int engine;
+    bool ladder;
+    int64_t batch, m, n, k;
+    double ms, flops, issued;
+  };
+  const std::vector<ProfLine>& profile_lines() const { return prof_lines_; }
+  std::vector<ProfLine> prof_lines_;
   double last_tc_issued = 0.0;  // MMA flops of the last tensor-core launch (padding included)
   struct CacheEntry;
   std::vector<CacheEntry*> cache_;

@@ -391,17 +391,24 @@ bool Executor::try_ladder(const Op& op) {
     wpm_.push_back(e);
     w = &wpm_.back();
   }
+  int pm_part = 0;  // 0: the + GEMM, 1: the - GEMM
   auto prof_begin = [&](ProfRec& rec) {
     if (!profiling_) return;
     cudaEventCreate(&rec.a);
     cudaEventCreate(&rec.b);
     cudaEventRecord(rec.a, st_);
     rec.flops = flops_each;
+    rec.m = nrows;
+    rec.n = np;
+    rec.k = np;
+    rec.label = op_label(op) + (pm_part == 0 ? " (pp-ladder, + pairs)" : " (pp-ladder, - pairs)");
+    pm_part ^= 1;
   };
   auto prof_end = [&](ProfRec& rec, bool tc) {
     if (!profiling_) return;
     cudaEventRecord(rec.b, st_);
     rec.tc = tc;
+    rec.engine = !tc ? 0 : mixed ? 1 : 2;
     rec.ladder = true;
     rec.issued = tc ? last_tc_issued : flops_each;
     prof_.push_back(rec);

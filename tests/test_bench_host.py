@@ -142,3 +142,24 @@ def test_reference_arm_loads_nothing_of_the_library(tmp_path):
     assert out["impl"] == "reference" and out["steps"] == 2 and out["steps_requested"] == 5
     assert out["value"] > 0 and out["cpu_baseline"]["kind"] == "oracle"
     assert "CLEAN" in r.stdout
+
+
+def test_contraction_table_sums_launches_per_step():
+    ns = runpy.run_path(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"))
+    rec = lambda label, ms, eng=1, lad=0: {"label": label, "engine": eng, "ladder": lad, "batch": 1, "m": 256,
+                                           "n": 128, "k": 64, "ms": ms, "flops": 2.0 * 256 * 128 * 64,
+                                           "issued_flops": 12.0 * 256 * 128 * 64}
+    # two steps of three launches: the ladder twice per step, a DFMA contraction once
+    recs = [rec("Y[ijab] += W[abcd] * X[ijcd] (pp-ladder, + pairs)", 4.0, lad=1),
+            rec("Y[ijab] += W[abcd] * X[ijcd] (pp-ladder, + pairs)", 4.0, lad=1),
+            rec("Z[ij] += F[ik] * X[kj]", 2.0, eng=0)] * 2
+    table = ns["contraction_table"](recs, 2, "test")
+    rows = [l for l in table.splitlines() if l.startswith("| `")]
+    assert len(rows) == 2
+    assert "pp-ladder" in rows[0] and "(ladder)" in rows[0]      # slowest first
+    cells = [c.strip() for c in rows[0].split("|")]
+    assert cells[4] == "2" and cells[5] == "8.00" and cells[6] == "80.0%"
+    # 2 M N K flops over 4 ms per launch
+    assert abs(float(cells[7]) - 2.0 * 256 * 128 * 64 / 4e-3 / 1e12) < 0.06
+    assert "FP64 DFMA" in rows[1] and "10.0 ms per step" in table
+    assert cells[9] == "0" and rows[1].rstrip().endswith("| — |")

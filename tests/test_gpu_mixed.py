@@ -8,6 +8,8 @@ transforms are compared element-wise with the oracle relative to the largest
 element: within 4e-4 for two slices and 2e-5 for three (the three-slice left
 transforms were measured at 5e-6 to 6.5e-6 on these inputs).
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -228,3 +230,44 @@ def test_thymine_adz_transforms_match_oracle_samples(precision):
         assert abs(pn - g["packed_norm"]) < tol * g["packed_norm"]
         # the plain sum over 5.66e7 elements cancels: bound by the per-element error times the count
         assert abs(float(y.sum()) - g["sum"]) < tol * g["maxabs"] * y.numel() ** 0.5 * 10
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_profile_records_account_for_every_gemm(prec):
+    """ccsd_profile_records: one record per GEMM launch, summing to the profile's totals."""
+    o, v, naux = 6, 48, 60
+    H = make_hamiltonian(o, v, naux, seed=4)
+    X1, X2 = random_amplitudes(o, v, 8, scale=0.03, nvec=3)
+    X = np.stack([flat(X1[i], X2[i]) for i in range(3)])
+    if prec == "mixed":
+        h = mixed(H, 3, tc_min_flops=1e6)
+    else:
+        h = B.ccsd_create(H.eps, H.h, H.B, o, v, naux, B.ccsd_default_options(precision=B.PREC_FP64))
+    try:
+        B.ccsd_set_amplitudes(h, X[0], np.zeros_like(X[0]))
+        Y = np.zeros_like(X)
+        B.ccsd_jacobian_transform(h, 0, 3, X, Y)  # first use: slices, autotuning
+        B.ccsd_profile_start(h)
+        B.ccsd_jacobian_transform(h, 0, 3, X, Y)
+        B.ccsd_jacobian_transform(h, 1, 3, X, Y)
+        tot = B.ccsd_profile_stop(h)
+        recs = B.ccsd_profile_records(h)
+        n = ctypes.c_int(0)
+        assert B.lib().ccsd_profile_records(h, None, -1, ctypes.byref(n)) == B.ERR_ARG
+        assert B.lib().ccsd_profile_records(h, None, 1, ctypes.byref(n)) == B.ERR_ARG
+        assert B.lib().ccsd_profile_records(h, None, 0, None) == B.ERR_ARG
+    finally:
+        B.ccsd_destroy(h)
+    assert len(recs) == tot["tc_launches"] + tot["fp64_launches"] > 0
+    tc = [r for r in recs if r["engine"] != B.GEMM_FP64]
+    assert len(tc) == tot["tc_launches"]
+    assert (len(tc) > 0) == (prec == "mixed")
+    assert abs(sum(r["ms"] for r in tc) - tot["tc_ms"]) < 1e-6 * max(tot["tc_ms"], 1.0)
+    assert abs(sum(r["flops"] for r in recs) - tot["tc_flops"] - tot["fp64_flops"]) < 1e-6 * sum(
+        r["flops"] for r in recs)
+    lad = [r for r in recs if r["ladder"]]
+    assert len(lad) == tot["ladder_launches"] == 4  # + and - pairs, right and left
+    for r in recs:
+        assert "+=" in r["label"] and r["ms"] >= 0.0 and r["m"] > 0 and r["n"] > 0 and r["k"] > 0
+        assert abs(r["flops"] - 2.0 * r["batch"] * r["m"] * r["n"] * r["k"]) < 1e-9 * r["flops"]
+        assert r["issued_flops"] >= r["flops"] * (0.999 if r["engine"] == B.GEMM_FP64 else 1.0)
