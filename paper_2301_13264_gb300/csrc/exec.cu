@@ -446,7 +446,7 @@ void Executor::exec_contract(const Op& op) {
 }
 
 void Executor::profile(bool on) {
-  if (!on) collect();
+  if (!on && !prof_.empty()) collect();  // records not yet collected (the last collect's lines stay)
   profiling_ = on;
 }
 
