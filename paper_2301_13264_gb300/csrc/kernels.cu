@@ -375,6 +375,78 @@ __global__ void k_drank1(GemmArgs g) {
   }
 }
 
+// Skinny shapes (N <= 16, the other extents large): C[b][m][n] = alpha sum_k A[b][m][k] B[b][n][k]
+// + beta C for all n at once, so that A is read once (the 64 x 64 tiles would pad N to 64).
+// The FP64 pipe bounds these (2 multiply-adds per clock per SM), so the kernel only has to keep
+// it busy with coalesced loads of A.
+//   ROWS = false: one 256-thread block per row m, the block's threads strided over k (A
+//                 contiguous along k, or neither way), then a fixed-order block reduction;
+//   ROWS = true:  one thread per row m, looping over k (A contiguous along m: the warp's loads
+//                 of A[m..m+31][k] coalesce, B[n][k] is the same for the warp).
+constexpr int SKINNY_N = 16;
+template <bool ROWS>
+__global__ void __launch_bounds__(256) k_dgemm_skinny(GemmArgs g) {
+  const int N = g.N;
+  if (!ROWS) {
+    __shared__ double red[8][SKINNY_N];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t rows = (int64_t)g.batch * g.M;
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+      const int64_t b = r / g.M, m = r % g.M;
+      const double* A = g.A + b * g.sAb + m * g.sAm;
+      const double* B = g.B + b * g.sBb;
+      double acc[SKINNY_N];
+#pragma unroll
+      for (int n = 0; n < SKINNY_N; ++n) acc[n] = 0.0;
+      for (int64_t k = threadIdx.x; k < g.K; k += blockDim.x) {
+        const double a = A[k * g.sAk];
+#pragma unroll
+        for (int n = 0; n < SKINNY_N; ++n)
+          if (n < N) acc[n] = fma(a, B[n * g.sBn + k * g.sBk], acc[n]);
+      }
+#pragma unroll
+      for (int n = 0; n < SKINNY_N; ++n) {
+        if (n >= N) break;
+        double v = acc[n];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) red[warp][n] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x < N) {
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
+        double* c = g.C + b * g.sCb + m * g.sCm + threadIdx.x * g.sCn;
+        *c = g.alpha * v + (g.beta != 0.0 ? g.beta * (*c) : 0.0);
+      }
+      __syncthreads();
+    }
+  } else {
+    const int64_t rows = (int64_t)g.batch * g.M;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t b = r / g.M, m = r % g.M;
+      const double* A = g.A + b * g.sAb + m * g.sAm;
+      const double* B = g.B + b * g.sBb;
+      double acc[SKINNY_N];
+#pragma unroll
+      for (int n = 0; n < SKINNY_N; ++n) acc[n] = 0.0;
+      for (int64_t k = 0; k < g.K; ++k) {
+        const double a = A[k * g.sAk];
+#pragma unroll
+        for (int n = 0; n < SKINNY_N; ++n)
+          if (n < N) acc[n] = fma(a, B[n * g.sBn + k * g.sBk], acc[n]);
+      }
+      double* c = g.C + b * g.sCb + m * g.sCm;
+#pragma unroll
+      for (int n = 0; n < SKINNY_N; ++n) {
+        if (n >= N) break;
+        c[n * g.sCn] = g.alpha * acc[n] + (g.beta != 0.0 ? g.beta * c[n * g.sCn] : 0.0);
+      }
+    }
+  }
+}
+
 static void launch_dgemm_chunk(const GemmArgs& g, cudaStream_t st) {
   if (g.K == 1) {
   count_launches(1);
@@ -402,6 +474,32 @@ static void launch_dgemm_chunk(const GemmArgs& g, cudaStream_t st) {
     t.sCm = g.sCn;
     t.sCn = g.sCm;
     k_dgemv<<<grid_for((int64_t)t.batch * t.M * 32), 256, 0, st>>>(t);
+    return;
+  }
+  // skinny: N (or M, with the roles of A and B swapped) at most 16, enough rows to fill the
+  // machine, K long enough that one pass over A dominates
+  if (std::min(g.M, g.N) <= SKINNY_N && (int64_t)std::max(g.M, g.N) * g.batch >= 512 && g.K >= 32) {
+    GemmArgs t = g;
+    if (g.M < g.N) {  // C^T = B A^T
+      t.M = g.N;
+      t.N = g.M;
+      t.A = g.B;
+      t.sAb = g.sBb;
+      t.sAm = g.sBn;
+      t.sAk = g.sBk;
+      t.B = g.A;
+      t.sBb = g.sAb;
+      t.sBn = g.sAm;
+      t.sBk = g.sAk;
+      t.sCm = g.sCn;
+      t.sCn = g.sCm;
+    }
+    const int64_t rows = (int64_t)t.batch * t.M;
+    count_launches(1);
+    if (t.sAm == 1 && t.sAk != 1)
+      k_dgemm_skinny<true><<<grid_for(rows), 256, 0, st>>>(t);
+    else
+      k_dgemm_skinny<false><<<(int)std::min<int64_t>(rows, 152 * 8), 256, 0, st>>>(t);
     return;
   }
   const int target = 2 * 152;

@@ -36,6 +36,7 @@
 
 #include "alloc.h"
 #include "exec.h"
+#include "tcgen05.cuh"
 
 namespace ccsd {
 
@@ -50,11 +51,11 @@ __global__ void k_pair_table(int v, int2* pairs) {
 __device__ __forceinline__ void put(bool bf16, int S, int64_t plane, __nv_bfloat16* d16, double* d64, int64_t at,
                                     double x) {
   if (bf16) {
-    for (int s = 0; s < S; ++s) {
-      __nv_bfloat16 b = __double2bfloat16(x);
-      d16[s * plane + at] = b;
-      x -= (double)__bfloat162float(b);
-    }
+    unsigned short q[3];
+    tc::split_bf16(x, S, q);  // integer and FP32 operations (the FP64 pipe issues 2 per clock per SM)
+#pragma unroll
+    for (int s = 0; s < 3; ++s)
+      if (s < S) d16[s * plane + at] = __ushort_as_bfloat16(q[s]);
   } else {
     d64[at] = x;
   }

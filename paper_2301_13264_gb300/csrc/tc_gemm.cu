@@ -374,15 +374,16 @@ __global__ void __launch_bounds__(256) k_split_gather(const double* __restrict__
       }
     }
     __syncthreads();
-    // split_bf16: integer and FP32 operations only (the FP64 pipe issues 2 per clock per SM)
+    // split_bf16x2: integer and FP32 operations only (the FP64 pipe issues 2 per clock per SM)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int rr = ty + 8 * i;
-      unsigned short q0[3], q1[3];
-      split_bf16(tile[rr][2 * tx], S, q0);
-      split_bf16(tile[rr][2 * tx + 1], S, q1);
+      unsigned int w[3];
+      split_bf16x2(tile[rr][2 * tx], tile[rr][2 * tx + 1], S, w);
       unsigned int* d = reinterpret_cast<unsigned int*>(dst + (r0 + rr) * Kp + k0 + 2 * tx);
-      for (int s = 0; s < S; ++s) d[s * (plane / 2)] = (unsigned int)q0[s] | ((unsigned int)q1[s] << 16);
+#pragma unroll
+      for (int s = 0; s < 3; ++s)
+        if (s < S) d[s * (plane / 2)] = w[s];
     }
     __syncthreads();
   }
@@ -552,6 +553,15 @@ static void launch_tc(dim3 grid, const CUtensorMap& ta, const CUtensorMap& tb, c
   tc::k_tc_gemm<BN><<<grid, tc::NTHREADS, tc::Cfg<BN>::SMEM_BYTES, st>>>(ta, tb, p);
 }
 
+// Output stride between consecutive indices of one side of a GEMM: the stride of that side's
+// fastest-varying dimension (offset table g), or the direct stride.
+static int64_t lane_stride(const Strided* g, int64_t direct) {
+  if (!g) return direct < 0 ? -direct : direct;
+  for (int d = g->ndim - 1; d >= 0; --d)
+    if (g->ext[d] > 1) return g->s0[d] < 0 ? -g->s0[d] : g->s0[d];
+  return 0;
+}
+
 bool Executor::tc_contract(int M, int N, int K, const double* A, const Strided& Ag, const double* B,
                            const Strided& Bg, double* C, int64_t sCm, int64_t sCn, double alpha, double beta,
                            bool a_const, bool b_const, const Strided* om, const Strided* on) {
@@ -561,6 +571,16 @@ bool Executor::tc_contract(int M, int N, int K, const double* A, const Strided& 
   Strided ag = Ag, bg = Bg;
   // the MMA tile is 128 rows of A by BN rows of B: put the longer side on A
   if (M < tc::BM && N > M) {
+    std::swap(M, N);
+    std::swap(A, B);
+    std::swap(ag, bg);
+    std::swap(a_const, b_const);
+    std::swap(sCm, sCn);
+    std::swap(om, on);
+  }
+  // the epilogue's 32 lanes hold 32 consecutive rows m: give the M side the output dimension
+  // with the smaller stride, so that their stores coalesce
+  if (N >= tc::BM && lane_stride(om, sCm) > lane_stride(on, sCn)) {
     std::swap(M, N);
     std::swap(A, B);
     std::swap(ag, bg);

@@ -132,61 +132,76 @@ inline int raster_group(int mt, int bn) {
   return mt < g ? mt : g;
 }
 
-// S bf16 slices of x (S = 2 or 3), x ~ out[0] + out[1] (+ out[2]), as the FP64 split
-// x_0 = bf16(x), x_1 = bf16(x - x_0), x_2 = bf16(x - x_0 - x_1) computes them, in integer and
-// FP32 operations only: x_0 is rounded (to nearest, ties to even) straight from the double's
-// bits, the remainder x - x_0 is formed exactly as an integer (at most 45 significant bits) and
-// rounded once to float (relative error 2^-24 of the remainder, 2^-32 of x), and the later
-// slices are split from that float, each FP32 remainder being exact.  Values outside the bf16
-// exponent range flush to zero or saturate to infinity; NaN gives NaN.
-__device__ __forceinline__ void split_bf16(double x, int S, unsigned short (&out)[3]) {
+// x as hi + lo in two floats, from the double's bits with 32-bit integer operations and one
+// integer-to-float conversion (no FP64 instruction: the FP64 pipe issues 2 per clock per SM).
+// hi keeps the top 24 significant bits of x (truncated), lo the remaining 29 bits, rounded
+// once to float: |x - hi - lo| <= 2^-47 |x|.  lo is dropped for |x| < 2^-74 (relative error
+// 2^-23 there), hi flushes to zero below the float normal range and saturates above it; Inf
+// and NaN go to hi with lo = 0.
+__device__ __forceinline__ void double_to_float2(double x, float& hi, float& lo) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-  const unsigned int sign16 = (unsigned int)(u >> 63) << 15;
-  const int E = (int)((u >> 52) & 0x7FFu);
-  out[0] = out[1] = out[2] = (unsigned short)sign16;
-  if (E == 0x7FF) {  // Inf or NaN: carried by the first slice
-    out[0] = (unsigned short)(sign16 | 0x7F80u | ((u & ((1ull << 52) - 1)) ? 0x40u : 0u));
+  const unsigned int w1 = (unsigned int)(u >> 32), w0 = (unsigned int)u;
+  const unsigned int sign = w1 & 0x80000000u;
+  const int E = (int)((w1 >> 20) & 0x7FFu);
+  const int fe = E - 1023 + 127;
+  lo = 0.0f;
+  if (E == 0x7FF) {  // Inf or NaN
+    hi = __uint_as_float(sign | 0x7F800000u | (((w1 & 0xFFFFFu) | w0) ? 0x400000u : 0u));
     return;
   }
-  const int ef = E - 1023 + 127;
-  if (E == 0 || ef <= 0) return;  // below the bf16 normal range
-  const unsigned long long M = (u & ((1ull << 52) - 1)) | (1ull << 52);  // 53-bit significand
-  unsigned long long q = M >> 45;                                          // 8 bits
-  const unsigned long long rest = M & ((1ull << 45) - 1), half = 1ull << 44;
-  if (rest > half || (rest == half && (q & 1ull))) ++q;
-  const long long d = (long long)M - (long long)(q << 45);  // x - x_0 = +-d 2^(E - 1075), |d| <= 2^44
-  const int e0 = (q == 256ull) ? ef + 1 : ef;
-  if (e0 >= 255) {
-    out[0] = (unsigned short)(sign16 | 0x7F80u);
+  if (fe <= 0) {
+    hi = __uint_as_float(sign);
     return;
   }
-  out[0] = (unsigned short)(sign16 | ((unsigned int)e0 << 7) | (unsigned int)(q == 256ull ? 0 : (q & 0x7Fu)));
-  if (d == 0) return;
-  // the remainder as a float: |d| rounded to 24 significant bits, exponent from its top bit
-  const unsigned long long a = (unsigned long long)(d < 0 ? -d : d);
-  const int p = 63 - __clzll((long long)a);  // a in [2^p, 2^(p+1)), p <= 44
-  unsigned long long mant;
-  int fe = p + (E - 1075) + 127;
-  if (p > 23) {
-    const int drop = p - 23;
-    mant = a >> drop;
-    const unsigned long long r2 = a & ((1ull << drop) - 1), h2 = 1ull << (drop - 1);
-    if (r2 > h2 || (r2 == h2 && (mant & 1ull))) ++mant;
-    if (mant == (1ull << 24)) {
-      mant >>= 1;
-      ++fe;
-    }
-  } else {
-    mant = a << (23 - p);
+  if (fe >= 255) {
+    hi = __uint_as_float(sign | 0x7F800000u);
+    return;
   }
-  if (fe <= 0) return;  // the remainder is below the float normal range
-  const unsigned int rsign = ((unsigned int)(u >> 63) ^ (d < 0 ? 1u : 0u)) << 31;
-  float r = __uint_as_float(rsign | ((unsigned int)fe << 23) | (unsigned int)(mant & ((1ull << 23) - 1)));
-  for (int s = 1; s < S; ++s) {
-    const __nv_bfloat16 b = __float2bfloat16_rn(r);
-    out[s] = __bfloat16_as_ushort(b);
-    r -= __bfloat162float(b);
+  hi = __uint_as_float(sign | ((unsigned int)fe << 23) | ((w1 & 0xFFFFFu) << 3) | (w0 >> 29));
+  const unsigned int low = w0 & 0x1FFFFFFFu;  // the bits below hi, in units of 2^(E - 1075)
+  if (low != 0u && E >= 949) {
+    const float scale = __uint_as_float((unsigned int)(E - 948) << 23);  // 2^(E - 1075), a normal float
+    lo = __uint_as_float(__float_as_uint(__uint2float_rn(low) * scale) | sign);
   }
+}
+
+// S bf16 slices of a pair of doubles (S = 2 or 3), x ~ slice 0 + slice 1 (+ slice 2), packed two
+// per word (xa in the low half): slice 0 = bf16(hi), slice 1 = bf16((hi - slice 0) + lo),
+// slice 2 = bf16 of that remainder, with (hi, lo) from double_to_float2.  Every FP32 remainder
+// hi - slice is exact; the sum with lo rounds at 2^-32 |x|, so the three slices carry x to
+// about 2^-26 |x| and two to 2^-17 |x|, the accuracy of the FP64 split x_0 = bf16(x),
+// x_1 = bf16(x - x_0), x_2 = bf16(x - x_0 - x_1).  Inf and NaN are carried by slice 0 alone.
+__device__ __forceinline__ void split_bf16x2(double xa, double xb, int S, unsigned int (&out)[3]) {
+  float ha, la, hb, lb;
+  double_to_float2(xa, ha, la);
+  double_to_float2(xb, hb, lb);
+  __nv_bfloat162 b = __floats2bfloat162_rn(ha, hb);
+  unsigned int w = *reinterpret_cast<unsigned int*>(&b);
+  out[0] = w;
+  // halves whose slice 0 is Inf or NaN (a non-finite x, or |x| beyond the bf16 range) keep
+  // zero later slices
+  const unsigned int finite = ((w & 0x7F80u) != 0x7F80u ? 0x0000FFFFu : 0u) |
+                              ((w & 0x7F800000u) != 0x7F800000u ? 0xFFFF0000u : 0u);
+  float ra = (ha - __uint_as_float(w << 16)) + la;
+  float rb = (hb - __uint_as_float(w & 0xFFFF0000u)) + lb;
+#pragma unroll
+  for (int s = 1; s < 3; ++s) {
+    if (s >= S) break;
+    b = __floats2bfloat162_rn(ra, rb);
+    w = *reinterpret_cast<unsigned int*>(&b) & finite;
+    out[s] = w;
+    ra -= __uint_as_float(w << 16);
+    rb -= __uint_as_float(w & 0xFFFF0000u);
+  }
+}
+
+// One double's S slices (the low halves of split_bf16x2).
+__device__ __forceinline__ void split_bf16(double x, int S, unsigned short (&out)[3]) {
+  unsigned int w[3] = {0u, 0u, 0u};
+  split_bf16x2(x, 0.0, S, w);
+  out[0] = (unsigned short)w[0];
+  out[1] = (unsigned short)w[1];
+  out[2] = (unsigned short)w[2];
 }
 
 // 3-D TMA map over bf16 slices [S][rows][Kp]: boxes of 64 K x box_rows rows x 1 slice,

@@ -271,3 +271,38 @@ def test_profile_records_account_for_every_gemm(prec):
         assert "+=" in r["label"] and r["ms"] >= 0.0 and r["m"] > 0 and r["n"] > 0 and r["k"] > 0
         assert abs(r["flops"] - 2.0 * r["batch"] * r["m"] * r["n"] * r["k"]) < 1e-9 * r["flops"]
         assert r["issued_flops"] >= r["flops"] * (0.999 if r["engine"] == B.GEMM_FP64 else 1.0)
+
+
+@pytest.mark.parametrize("S,bits", [(2, 15), (3, 20)])
+def test_split_products_of_single_terms(S, bits):
+    """K = 1: C = a b^T through the split-bf16 products, operands over 2^-30..2^31 (products far
+    inside the FP32 normal range), both signs, carries out of the rounding and zeros.  Each
+    element is the FP32 sum of the S(S+1)/2 slice products of one a_m and one b_n: within
+    about 2^-15 (two slices) and 2^-20 (three slices: the dropped products 2^-24 each plus
+    five FP32 roundings) of |a_m b_n|."""
+    rng = np.random.default_rng(11)
+    sgn = lambda n: np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    a = sgn(300) * rng.uniform(1.0, 2.0, 300) * 2.0 ** rng.integers(-30, 30, 300)
+    b = sgn(200) * rng.uniform(1.0, 2.0, 200) * 2.0 ** rng.integers(-30, 30, 200)
+    a[:8] = [1.0, -2.0 ** -30, np.nextafter(2.0, 0.0), -(1.0 - 2.0 ** -53), 0.0, -0.0, 1.0 + 2.0 ** -23,
+             -(2.0 ** 24 - 1.0) * 2.0 ** -50]
+    C, _ = B.ccsd_gemm(B.GEMM_SPLIT, a[:, None], b[:, None], splits=S)
+    ref = np.outer(a, b)
+    assert np.all(np.abs(C - ref) <= 2.0 ** -bits * np.abs(ref)), (np.abs(C - ref) / np.abs(ref)).max()
+
+
+def test_three_slices_carry_the_bits_below_float():
+    """Rows [a_m, -fl32(a_m)] against [1, 1]: fl32(a_m) has 24 significant bits, which three
+    slices carry exactly, and the slice products of each level nearly cancel and sum exactly,
+    so C_m = a_m - fl32(a_m) + (the three slices' error in a_m).  That error is at most
+    2^-26 |a_m| for the split from the double's bits (2^-28 rms), while a_m - fl32(a_m) is up
+    to 2^-24 |a_m|: a split that rounded a_m to float first would miss by that much."""
+    rng = np.random.default_rng(12)
+    a = (np.where(rng.random(4000) < 0.5, -1.0, 1.0) * rng.uniform(1.0, 2.0, 4000)
+         * 2.0 ** rng.integers(-50, 50, 4000))
+    A = np.stack([a, -a.astype(np.float32).astype(np.float64)], axis=1)
+    C, _ = B.ccsd_gemm(B.GEMM_SPLIT, A, np.ones((1, 2)), splits=3)
+    ref = a - a.astype(np.float32).astype(np.float64)
+    err = np.abs(C[:, 0] - ref) / np.abs(a)
+    assert err.max() <= 2.0 ** -25, err.max()
+    assert (np.abs(ref) / np.abs(a)).max() > 2.0 ** -24.5  # the test would see a lost remainder
