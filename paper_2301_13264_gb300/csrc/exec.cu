@@ -277,11 +277,35 @@ void Executor::exec_contract(const Op& op) {
       }
       return g;
     };
-    Strided ag = gather(ea, Ml), bg = gather(eb, Nl);
     // amplitude-dependent operands are cached only in runs that leave all of them unchanged
     // (the derivative programs), not in the forward program that recomputes them
     auto cacheable = [&](int t) { return const_tensors.count(t) > 0 || (frozen_tensors.count(t) > 0 && !frozen_run_); };
     const bool a_const = cacheable(op.a.t), b_const = cacheable(op.b.t);
+    // The gather of an operand sliced anew at every call reads coalesced only if its last K
+    // label or its last row label is contiguous in it.  When neither is but another row label
+    // is, and the operand outweighs the output, that label goes last in the row order (the
+    // output follows the same order through its offset table).
+    std::vector<char> Mt = Ml, Nt = Nl;
+    auto unit = [](std::map<char, std::pair<int64_t, int64_t>>& es, char c) {
+      return es[c].first > 1 && (es[c].second == 1 || es[c].second == -1);
+    };
+    auto favor = [&](std::vector<char>& rows, std::map<char, std::pair<int64_t, int64_t>>& es, int64_t nrows,
+                     bool cached) {
+      if (cached || rows.size() < 2 || (double)nrows * K < 2.0 * (double)M * N) return false;
+      if ((!Kl.empty() && unit(es, Kl.back())) || unit(es, rows.back())) return false;
+      for (size_t i = 0; i + 1 < rows.size(); ++i)
+        if (unit(es, rows[i])) {
+          const char c = rows[i];
+          rows.erase(rows.begin() + i);
+          rows.push_back(c);
+          return true;
+        }
+      return false;
+    };
+    const bool reordered_a = favor(Mt, ea, M, a_const);
+    const bool reordered_b = favor(Nt, eb, N, b_const);
+    const bool cdir = cdirect && !reordered_a && !reordered_b;
+    Strided ag = gather(ea, Mt), bg = gather(eb, Nt);
     // non-contiguous outputs are addressed by the GEMM epilogue through the output's own strides
     Strided om, on;
     auto out_dims = [&](const std::vector<char>& labels, Strided& g) {
@@ -297,9 +321,9 @@ void Executor::exec_contract(const Op& op) {
         g.s0[0] = g.s1[0] = 0;
       }
     };
-    if (!cdirect) {
-      out_dims(Ml, om);
-      out_dims(Nl, on);
+    if (!cdir) {
+      out_dims(Mt, om);
+      out_dims(Nt, on);
     }
     double* Ct = nullptr;
     ProfRec rec{};
@@ -315,9 +339,8 @@ void Executor::exec_contract(const Op& op) {
       rec.k = K;
       rec.label = op_label(op);
     }
-    bool ok = tc_contract((int)M, (int)N, (int)K, A.base, ag, B.base, bg, O.base, cdirect ? sCm : 0,
-                          cdirect ? sCn : 0, op.alpha, 1.0, a_const, b_const, cdirect ? nullptr : &om,
-                          cdirect ? nullptr : &on);
+    bool ok = tc_contract((int)M, (int)N, (int)K, A.base, ag, B.base, bg, O.base, cdir ? sCm : 0, cdir ? sCn : 0,
+                          op.alpha, 1.0, a_const, b_const, cdir ? nullptr : &om, cdir ? nullptr : &on);
     if (profiling_) {
       CK(cudaEventRecord(rec.b, st_));
       rec.tc = ok;

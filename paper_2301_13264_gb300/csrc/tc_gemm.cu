@@ -42,7 +42,7 @@ namespace ccsd {
 
 namespace tc {
 
-constexpr int NTHREADS = 192;  // TMA warp, MMA warp, 4 epilogue warps
+constexpr int NTHREADS = 320;  // TMA warp, MMA warp, two groups of 4 epilogue warps
 constexpr int A_BYTES = BM * BK * 2;
 // per tile width BN (64, 128 or 256): B tile bytes, pipeline depth, shared memory
 template <int BN>
@@ -50,8 +50,9 @@ struct Cfg {
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
   static constexpr int STAGES = (BN == 256) ? 4 : 6;
-  // stages, the strided-output column offsets [BN], barriers; 1 KB alignment slack
-  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + BN * 8 + 256 + 1024;
+  // stages, the strided-output column offsets [2][BN] (one row per epilogue group), barriers;
+  // 1 KB alignment slack
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 2 * BN * 8 + 256 + 1024;
 };
 constexpr int MAXPROD = 6;
 
@@ -88,8 +89,9 @@ __device__ __forceinline__ long long dim_offset(long long x, const Strided& g) {
   return off;
 }
 
-// Named barrier among the 128 epilogue threads (warps 2..5); barrier 0 is __syncthreads.
-__device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Named barrier among the 128 threads of epilogue group g (warps 2..5: barrier 1, warps 6..9:
+// barrier 2); barrier 0 is __syncthreads.
+__device__ __forceinline__ void epilogue_sync(int g) { asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory"); }
 
 __device__ __forceinline__ void mbar_arrive1(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -99,9 +101,11 @@ __device__ __forceinline__ void mbar_arrive1(uint32_t bar) {
 // w = blockIdx.x, blockIdx.x + gridDim.x, ... of (split z, output tile) in raster order.
 // Warp 0 lane 0 loads A and B K-tiles by TMA into the STAGES-deep ring; warp 1 lane 0
 // issues the MMAs of an item into one of two TMEM accumulators (columns b*BN, b = item
-// parity) and commits acc_full[b]; warps 2..5 read the finished accumulator (warp w owns
-// TMEM lanes 32 (w % 4) ..), release it with acc_empty[b] and write the FP64 output while
-// the MMA warp already fills the other accumulator for the next item.
+// parity) and commits acc_full[b]; epilogue group b (warps 2..5 for b = 0, 6..9 for b = 1)
+// reads the finished accumulator b (warp w owns TMEM lanes 32 (w % 4) ..), releases it with
+// acc_empty[b] and writes the FP64 output.  The two groups write two tiles at once, doubling
+// the loads and stores in flight for GEMMs whose output traffic decides their time, while
+// the MMA warp fills whichever accumulator is free.
 template <int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, Params p) {
@@ -112,8 +116,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
-  long long* coloff = reinterpret_cast<long long*>(smem + STAGES * STAGE_BYTES);  // [BN]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + BN * sizeof(long long));
+  long long* coloff = reinterpret_cast<long long*>(smem + STAGES * STAGE_BYTES);  // [2][BN]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + 2 * BN * sizeof(long long));
   uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 5);
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
   const uint32_t accf0 = smem_u32(bars + 2 * STAGES), acce0 = smem_u32(bars + 2 * STAGES + 2);
@@ -233,11 +237,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     __syncwarp();
   } else {
-    // ---- epilogue: warps 2..5, TMEM lanes 32 (warp % 4) ----
+    // ---- epilogue: group g = warps 2..5 (g = 0) or 6..9 (g = 1), the items of parity g,
+    //      TMEM lanes 32 (warp % 4) of accumulator g ----
+    const int g = (warp - 2) >> 2;
     const int lane_base = 32 * (warp & 3);
-    const int et = threadIdx.x - 64;  // 0..127
-    int item = 0;
-    for (int w = blockIdx.x; w < items; w += gridDim.x, ++item) {
+    const int et = threadIdx.x - 64 - 128 * g;  // 0..127
+    long long* gcol = coloff + g * BN;
+    int item = g;
+    for (int w = blockIdx.x + g * gridDim.x; w < items; w += 2 * gridDim.x, item += 2) {
       int tm, tn, it0, it1;
       raster_tile(w % tiles, p.mt, p.nt, p.group_m, tm, tn);
       k_range(w, it0, it1);
@@ -248,13 +255,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const bool split = p.nsplit > 1;
       const bool ostr = !split && p.ostr;
       // column offsets of a strided output for this tile (the previous tile's are no longer read)
-      epilogue_sync();
+      epilogue_sync(g);
       if (ostr)
-        for (int c = et; c < BN; c += 128) coloff[c] = (n0 + c < p.N) ? dim_offset(n0 + c, p.on) : 0;
-      epilogue_sync();
+        for (int c = et; c < BN; c += 128) gcol[c] = (n0 + c < p.N) ? dim_offset(n0 + c, p.on) : 0;
+      epilogue_sync(g);
       // the accumulator wait spans the item's whole mainloop: default bound.  On failure the
-      // four warps do not leave the loop (they would then disagree on the named barriers
-      // above): they keep walking the items with every wait failing fast on the raised flag.
+      // group's four warps do not leave the loop (they would then disagree on the named
+      // barrier above): they keep walking the items with every wait failing fast on the flag.
       const bool ready = mbar_wait(accf0 + 8 * b, use, err);
       if (!ready) atomicExch((int*)p.err, 1);
       fence_after();
@@ -283,7 +290,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
               const int n = n0 + c + j;
-              old[j] = (n < p.N) ? crow[ostr ? coloff[c + j] : (long long)n * cs] : 0.0;
+              old[j] = (n < p.N) ? crow[ostr ? gcol[c + j] : (long long)n * cs] : 0.0;
             }
           }
 #pragma unroll
@@ -291,7 +298,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             const int n = n0 + c + j;
             if (n < p.N) {
               const double v = empty ? 0.0 : p.alpha * (double)__uint_as_float(r[j]);
-              crow[ostr ? coloff[c + j] : (long long)n * cs] = acc ? old[j] + v : v;
+              crow[ostr ? gcol[c + j] : (long long)n * cs] = acc ? old[j] + v : v;
             }
           }
         }
