@@ -381,8 +381,9 @@ __global__ void k_drank1(GemmArgs g) {
 // it busy with coalesced loads of A.
 //   ROWS = false: one 256-thread block per row m, the block's threads strided over k (A
 //                 contiguous along k, or neither way), then a fixed-order block reduction;
-//   ROWS = true:  one thread per row m, looping over k (A contiguous along m: the warp's loads
-//                 of A[m..m+31][k] coalesce, B[n][k] is the same for the warp).
+//   ROWS = true:  32 rows per block, one per lane, the block's 8 warps strided over k (A
+//                 contiguous along m: the warp's loads of A[m..m+31][k] coalesce, B[n][k] is
+//                 the same for the warp), then a fixed-order reduction over the warps.
 constexpr int SKINNY_N = 16;
 template <bool ROWS>
 __global__ void __launch_bounds__(256) k_dgemm_skinny(GemmArgs g) {
@@ -423,26 +424,44 @@ __global__ void __launch_bounds__(256) k_dgemm_skinny(GemmArgs g) {
       __syncthreads();
     }
   } else {
+    // 32 rows per block (one per lane), the 8 warps strided over k, partial sums reduced in a
+    // fixed order through shared memory
+    __shared__ double red[8][SKINNY_N][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t rows = (int64_t)g.batch * g.M;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
-      const int64_t b = r / g.M, m = r % g.M;
-      const double* A = g.A + b * g.sAb + m * g.sAm;
-      const double* B = g.B + b * g.sBb;
+    for (int64_t r0 = (int64_t)blockIdx.x * 32; r0 < rows; r0 += (int64_t)gridDim.x * 32) {
+      const int64_t r = r0 + lane;
       double acc[SKINNY_N];
 #pragma unroll
       for (int n = 0; n < SKINNY_N; ++n) acc[n] = 0.0;
-      for (int64_t k = 0; k < g.K; ++k) {
-        const double a = A[k * g.sAk];
+      if (r < rows) {
+        const int64_t b = r / g.M, m = r % g.M;
+        const double* A = g.A + b * g.sAb + m * g.sAm;
+        const double* B = g.B + b * g.sBb;
+        for (int64_t k = warp; k < g.K; k += 8) {
+          const double a = A[k * g.sAk];
 #pragma unroll
-        for (int n = 0; n < SKINNY_N; ++n)
-          if (n < N) acc[n] = fma(a, B[n * g.sBn + k * g.sBk], acc[n]);
+          for (int n = 0; n < SKINNY_N; ++n)
+            if (n < N) acc[n] = fma(a, B[n * g.sBn + k * g.sBk], acc[n]);
+        }
       }
-      double* c = g.C + b * g.sCb + m * g.sCm;
 #pragma unroll
-      for (int n = 0; n < SKINNY_N; ++n) {
-        if (n >= N) break;
-        c[n * g.sCn] = g.alpha * acc[n] + (g.beta != 0.0 ? g.beta * c[n * g.sCn] : 0.0);
+      for (int n = 0; n < SKINNY_N; ++n)
+        if (n < N) red[warp][n][lane] = acc[n];
+      __syncthreads();
+      for (int q = threadIdx.x; q < N * 32; q += blockDim.x) {
+        const int n = q >> 5, l = q & 31;
+        const int64_t rr = r0 + l;
+        if (rr < rows) {
+          double v = 0.0;
+#pragma unroll
+          for (int w = 0; w < 8; ++w) v += red[w][n][l];
+          const int64_t b = rr / g.M, m = rr % g.M;
+          double* c = g.C + b * g.sCb + m * g.sCm + n * g.sCn;
+          *c = g.alpha * v + (g.beta != 0.0 ? g.beta * (*c) : 0.0);
+        }
       }
+      __syncthreads();
     }
   }
 }
@@ -497,7 +516,7 @@ static void launch_dgemm_chunk(const GemmArgs& g, cudaStream_t st) {
     const int64_t rows = (int64_t)t.batch * t.M;
     count_launches(1);
     if (t.sAm == 1 && t.sAk != 1)
-      k_dgemm_skinny<true><<<grid_for(rows), 256, 0, st>>>(t);
+      k_dgemm_skinny<true><<<(int)std::min<int64_t>((rows + 31) / 32, 152 * 8), 256, 0, st>>>(t);
     else
       k_dgemm_skinny<false><<<(int)std::min<int64_t>(rows, 152 * 8), 256, 0, st>>>(t);
     return;

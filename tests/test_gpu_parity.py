@@ -193,14 +193,29 @@ def test_error_statuses():
 
 
 def test_thymine_dz_residual_and_transforms_full_size():
-    """Thymine/cc-pVDZ-shaped system (o=33, v=123, naux=550): element-wise parity."""
+    """Thymine/cc-pVDZ-shaped system (o=33, v=123, naux=550): the FP64 residual and a block of
+    two right and left Jacobian transforms at given amplitudes, element-wise against the
+    oracle (every FP64 GEMM shape of the transform programs at full size, the skinny
+    nvec-wide ones included)."""
     H = workload("thymine_dz")
     o, v = H.o, H.v
-    x1, x2 = random_amplitudes(o, v, 4, scale=0.01, nvec=2)
+    x1, x2 = random_amplitudes(o, v, 4, scale=0.01, nvec=3)
     t = flat(x1[0], x2[0])
+    X = np.stack([flat(x1[k], x2[k]) * 10.0 for k in (1, 2)])
     om = np.zeros_like(t)
+    YR, YL = np.zeros_like(X), np.zeros_like(X)
     with Handle(H) as hd:
         e = B.ccsd_residual(hd.h, t, om)
+        B.ccsd_set_amplitudes(hd.h, t, np.zeros_like(t))
+        B.ccsd_jacobian_transform(hd.h, 0, 2, X, YR)
+        B.ccsd_jacobian_transform(hd.h, 1, 2, X, YL)
     c1, c2, ce = cc.residual(cc.as_t(x1[0]), cc.as_t(x2[0]), cc.as_t(H.h), cc.as_t(H.B), o)
     assert relerr(om, flat(c1, c2)) < 1e-11
     assert abs(e - float(ce)) < 1e-9
+    S = System(H.eps, H.h, H.B, o, vvvv_batch=16)
+    tv = Vec(cc.as_t(x1[0]), cc.as_t(x2[0]))
+    for k, side in ((0, "right"), (1, "right"), (0, "left")):
+        r = Vec(*map(cc.as_t, split(X[k], o, v)))
+        ref = S.right(tv, r) if side == "right" else S.left(tv, r)
+        got = (YR if side == "right" else YL)[k]
+        assert relerr(got, flat(ref.x1, ref.x2)) < 1e-11, (k, side)
