@@ -52,6 +52,8 @@ def parse():
                          "for the comma-separated forms among mixed, fp64, fp64tc ('both' = mixed,fp64)")
     ap.add_argument("--tol-eom", type=float, default=1e-8, help="--ttc: EOM residual-norm threshold")
     ap.add_argument("--max-sub", type=int, default=48, help="--ttc: Davidson subspace size before a restart")
+    ap.add_argument("--ttc-profile", action="store_true",
+                    help="--ttc: add the GEMM device time per arithmetic form (events around every GEMM)")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead of the single-system bench, time batched transforms of this many small systems")
     ap.add_argument("--no-autotune", action="store_true", help="batch mode: tile widths from the output width")
@@ -492,11 +494,25 @@ def run_ttc(args):
     linear).  Every form is compared, root by root, with the FP64 DFMA form when
     it ran, else with the FP64-grade tensor-core form."""
     forms = ["mixed", "fp64"] if args.ttc == "both" else args.ttc.split(",")
-    print(json.dumps(measure_ttc(args.workload, forms, args.splits, args.tol_eom, args.max_sub)), flush=True)
+    print(json.dumps(measure_ttc(args.workload, forms, args.splits, args.tol_eom, args.max_sub, args.ttc_profile)),
+          flush=True)
 
 
-def measure_ttc(workload_name, forms, splits, tol_eom, max_sub):
-    """The time-to-converged-coupling comparison of run_ttc as a dict."""
+def gemm_time_by_engine(records) -> dict:
+    """GEMM launches, device milliseconds and algorithmic TFLOP per arithmetic form."""
+    out = {}
+    for r in records:
+        e = out.setdefault(ENGINES.get(r["engine"], str(r["engine"])), {"launches": 0, "ms": 0.0, "alg_tflop": 0.0})
+        e["launches"] += 1
+        e["ms"] += r["ms"]
+        e["alg_tflop"] += r["flops"] / 1e12
+    return out
+
+
+def measure_ttc(workload_name, forms, splits, tol_eom, max_sub, profile=False):
+    """The time-to-converged-coupling comparison of run_ttc as a dict.  With profile, every
+    GEMM after ccsd_create is bracketed by CUDA events (which slows the run a little) and the
+    device time per arithmetic form is added."""
     import torch
     from paper_2301_13264_gb300 import binding as B
     from paper_2301_13264_gb300.synth import workload
@@ -515,6 +531,8 @@ def measure_ttc(workload_name, forms, splits, tol_eom, max_sub):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = B.ccsd_create(H.eps, H.h, H.B, H.o, H.v, H.naux, opt)
+        if profile:
+            B.ccsd_profile_start(h)
         e, it_g = B.ccsd_solve_ground(h)
         t_g = time.perf_counter() - t0
         print(f"[ttc {form}] ground {t_g:.1f}s {it_g} iterations E={e:.12f}", file=sys.stderr, flush=True)
@@ -529,6 +547,9 @@ def measure_ttc(workload_name, forms, splits, tol_eom, max_sub):
         out["forms"][form] = {"seconds": t, "ground_s": t_g, "eom_s": t_e - t_g, "couplings_s": t - t_e,
                               "e_ccsd": e, "omega": w, "F": F, "iters": [it_g, it_r, it_l],
                               "stats": B.ccsd_stats(h)}
+        if profile:
+            B.ccsd_profile_stop(h)
+            out["forms"][form]["gemm_time"] = gemm_time_by_engine(B.ccsd_profile_records(h))
         B.ccsd_destroy(h)
     out["thresholds"] = {"tol_res": 1e-10, "tol_eom": tol_eom, "tol_lin": 1e-9, "davidson_max_sub": max_sub}
     ref_name = "fp64" if "fp64" in out["forms"] else ("fp64tc" if "fp64tc" in out["forms"] else None)

@@ -98,11 +98,18 @@ def test_time_to_coupling_json(monkeypatch, capsys):
     monkeypatch.setattr(B, "ccsd_stats", lambda h: {"flops_fp64": 1.0, "flops_tc": 2.0, "gemms": 3, "tc_gemms": 4})
     monkeypatch.setattr(B, "ccsd_destroy", lambda h: None)
     monkeypatch.setattr(synth, "workload", lambda name: synth.make_hamiltonian(2, 4, 6, seed=0))
-    monkeypatch.setattr(sys, "argv", ["bench.py", "--ttc", "mixed,fp64tc,fp64", "--workload", "thymine_dz"])
+    monkeypatch.setattr(B, "ccsd_profile_start", lambda h: None)
+    monkeypatch.setattr(B, "ccsd_profile_stop", lambda h: {})
+    monkeypatch.setattr(B, "ccsd_profile_records", lambda h: [
+        {"engine": 1, "ms": 2.0, "flops": 4e12}, {"engine": 2, "ms": 1.0, "flops": 1e12},
+        {"engine": 1, "ms": 3.0, "flops": 1e12}])
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--ttc", "mixed,fp64tc,fp64", "--workload", "thymine_dz",
+                                      "--ttc-profile"])
     runpy.run_path(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "bench.py"),
                    run_name="__main__")
     out = json.loads([l for l in capsys.readouterr().out.splitlines() if l.startswith("{")][0])
     assert created == [B.PREC_MIXED, B.PREC_FP64_TC, B.PREC_FP64]
+    assert out["forms"]["mixed"]["gemm_time"]["split-bf16 TC"] == {"launches": 2, "ms": 5.0, "alg_tflop": 5.0}
     assert set(out["forms"]) == {"mixed", "fp64tc", "fp64"}
     for form in ("mixed", "fp64tc"):
         cmp = out["forms"][form]["vs_fp64"]
