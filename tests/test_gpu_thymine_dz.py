@@ -1,0 +1,85 @@
+"""Full-size parity on the thymine/cc-pVDZ-shaped system (o=33, v=123, naux=550, a 0.25 Eh gap
+between the two lowest virtual orbitals) against the oracle's stored FP64 results.
+
+tests/golden/make_thymine_dz.py runs the oracle's whole pipeline (ground state to 1e-11,
+Lambda and zeta to 1e-10, four EOM roots to a residual norm of 1e-9) and stores E_CCSD, the
+four omega_k and the derivative couplings F_kl of Eq. NAC_NC along (h1, B1) for ordered pairs
+of {0, 1, 2, 3, 4}, rewriting the file after each coupling; these tests compare what the file
+holds.  The GPU forms must match within the method's FP64 tolerances: 1e-8 Eh on the energy,
+1e-8 on excitation energies and 1e-7 relative on couplings.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2301_13264_gb300 import binding as B
+from paper_2301_13264_gb300.synth import workload
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "thymine_dz.json")
+TOL = dict(tol_res=1e-10, tol_eom=1e-9, tol_lin=1e-10, max_iter=200, davidson_max_sub=96)
+
+
+@pytest.fixture(scope="module")
+def golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+def run_form(golden, pairs, **opt):
+    """E, the roots (when the file holds them) and the couplings of `pairs` in one handle."""
+    H = workload("thymine_dz")
+    h = B.ccsd_create(H.eps, H.h, H.B, H.o, H.v, H.naux, B.ccsd_default_options(**TOL, **opt))
+    try:
+        e, _ = B.ccsd_solve_ground(h)
+        w, F = None, {}
+        if "omega" in golden:
+            w, _ = B.eom_solve_right(h, golden["nroots"])
+            B.eom_solve_left(h, golden["nroots"])
+            F = {kl: B.ccsd_derivative_coupling(h, kl[0], kl[1], 1, H.h1, H.B1)[0] for kl in pairs}
+    finally:
+        B.ccsd_destroy(h)
+    return e, w, F
+
+
+def check(golden, e, w, F):
+    assert abs(e - golden["e_ccsd"]) < 1e-8, (e, golden["e_ccsd"])
+    if w is not None:
+        assert np.abs(np.array(w) - np.array(golden["omega"])).max() < 1e-8, (w, golden["omega"])
+    for kl, f in F.items():
+        ref = golden["F"][f"{kl[0]},{kl[1]}"]
+        assert abs(f - ref) < 1e-7 * abs(ref), (kl, f, ref)
+
+
+def stored_pairs(golden, limit=None):
+    pairs = [tuple(int(x) for x in k.split(",")) for k in golden["F"]]
+    return pairs[:limit] if limit else pairs
+
+
+def test_thymine_dz_refined_mixed_matches_oracle(golden):
+    """Split-bf16 tensor-core products with FP64 refinement of every solve: the energy, the four
+    roots and every stored coupling."""
+    e, w, F = run_form(golden, stored_pairs(golden), precision=B.PREC_MIXED, splits=3)
+    check(golden, e, w, F)
+
+
+def test_thymine_dz_fp64_grade_matches_oracle(golden):
+    """Every contraction as FP64-grade tensor-core products, solved directly to the FP64
+    tolerances: the energy, the four roots and up to four stored couplings."""
+    e, w, F = run_form(golden, stored_pairs(golden, 4), precision=B.PREC_FP64_TC)
+    check(golden, e, w, F)
+
+
+def test_thymine_dz_fp64_ground_state_matches_oracle(golden):
+    """The plain FP64 (DFMA) form's ground-state energy (its EOM roots at this size take minutes
+    each; the FP64-grade form above covers them)."""
+    H = workload("thymine_dz")
+    h = B.ccsd_create(H.eps, H.h, H.B, H.o, H.v, H.naux, B.ccsd_default_options(**TOL))
+    try:
+        e, _ = B.ccsd_solve_ground(h)
+    finally:
+        B.ccsd_destroy(h)
+    assert abs(e - golden["e_ccsd"]) < 1e-8
