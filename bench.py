@@ -52,6 +52,8 @@ def parse():
                          "for the comma-separated forms among mixed, fp64, fp64tc ('both' = mixed,fp64)")
     ap.add_argument("--tol-eom", type=float, default=1e-8, help="--ttc: EOM residual-norm threshold")
     ap.add_argument("--max-sub", type=int, default=48, help="--ttc: Davidson subspace size before a restart")
+    ap.add_argument("--tc-min-flops", type=float, default=None,
+                    help="--ttc: smallest contraction (flops) run on the tensor cores (library default 2e9)")
     ap.add_argument("--ttc-profile", action="store_true",
                     help="--ttc: add the GEMM device time per arithmetic form (events around every GEMM)")
     ap.add_argument("--batch", type=int, default=0,
@@ -494,8 +496,8 @@ def run_ttc(args):
     linear).  Every form is compared, root by root, with the FP64 DFMA form when
     it ran, else with the FP64-grade tensor-core form."""
     forms = ["mixed", "fp64"] if args.ttc == "both" else args.ttc.split(",")
-    print(json.dumps(measure_ttc(args.workload, forms, args.splits, args.tol_eom, args.max_sub, args.ttc_profile)),
-          flush=True)
+    print(json.dumps(measure_ttc(args.workload, forms, args.splits, args.tol_eom, args.max_sub, args.ttc_profile,
+                                 args.tc_min_flops)), flush=True)
 
 
 def gemm_time_by_engine(records) -> dict:
@@ -509,7 +511,7 @@ def gemm_time_by_engine(records) -> dict:
     return out
 
 
-def measure_ttc(workload_name, forms, splits, tol_eom, max_sub, profile=False):
+def measure_ttc(workload_name, forms, splits, tol_eom, max_sub, profile=False, tc_min_flops=None):
     """The time-to-converged-coupling comparison of run_ttc as a dict.  With profile, every
     GEMM after ccsd_create is bracketed by CUDA events (which slows the run a little) and the
     device time per arithmetic form is added."""
@@ -526,8 +528,9 @@ def measure_ttc(workload_name, forms, splits, tol_eom, max_sub, profile=False):
            "forms": {}}
     for form in forms:
         prec = precision_of(form)
+        kw = {} if tc_min_flops is None else {"tc_min_flops": tc_min_flops}
         opt = B.ccsd_default_options(precision=prec, splits=splits, tol_res=1e-10, tol_eom=tol_eom,
-                                     tol_lin=1e-9, max_iter=300, refine=1, davidson_max_sub=max_sub)
+                                     tol_lin=1e-9, max_iter=300, refine=1, davidson_max_sub=max_sub, **kw)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = B.ccsd_create(H.eps, H.h, H.B, H.o, H.v, H.naux, opt)
