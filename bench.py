@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--tol-eom", type=float, default=1e-8, help="--ttc: EOM residual-norm threshold")
     ap.add_argument("--max-sub", type=int, default=48, help="--ttc: Davidson subspace size before a restart")
     ap.add_argument("--tc-min-flops", type=float, default=None,
-                    help="--ttc: smallest contraction (flops) run on the tensor cores (library default 2e9)")
+                    help="--ttc: smallest contraction (flops) run on the tensor cores (library default 1e8)")
     ap.add_argument("--ttc-profile", action="store_true",
                     help="--ttc: add the GEMM device time per arithmetic form (events around every GEMM)")
     ap.add_argument("--batch", type=int, default=0,

@@ -82,7 +82,7 @@ typedef struct {
   int davidson_max_sub; /* subspace size before restart */
   int guess;            /* CCSD_GUESS_MP2 */
   void* stream;         /* cudaStream_t, 0 = default */
-  double tc_min_flops;  /* mixed mode: contractions below this many flops stay FP64 */
+  double tc_min_flops;  /* contractions below this many flops stay FP64 DFMA (default 1e8) */
   int refine;           /* mixed mode: 1 = refine every solve to the FP64 tolerances above (FP64 residuals
                            with mixed-precision correction solves); 0 = stop at the mixed-precision floor */
   double tol_switch;    /* mixed mode with refine: residual level at which the FP64 refinement starts */

@@ -1388,7 +1388,7 @@ void ccsd_default_options(ccsd_options* opt) {
   opt->davidson_max_sub = 48;
   opt->guess = CCSD_GUESS_MP2;
   opt->stream = nullptr;
-  opt->tc_min_flops = 2.0e9;
+  opt->tc_min_flops = 1.0e8;
   opt->refine = 1;
   opt->tol_switch = 1e-6;
   opt->autotune = 0;

@@ -64,7 +64,7 @@ class Executor {
   // widths and split counts once per GEMM shape and keep the fastest
   int autotune = 0;
   // contractions with fewer flops than this stay on the FP64 path in mixed mode
-  double tc_min_flops = 2.0e9;
+  double tc_min_flops = 1.0e8;
   // clock cycles a pipeline wait of a tensor-core kernel may take before the kernel
   // raises the error flag and exits (0: the default bound, about 2 s)
   long long wait_cycles = 0;

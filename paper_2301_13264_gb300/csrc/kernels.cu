@@ -1,6 +1,7 @@
 // FP64 kernels: strided permute/accumulate, batched DFMA GEMM, amplitude-vector
 // operations (packed inner products, preconditioner, pair symmetrisation).
 #include "kernels.cuh"
+#include "fpsplit.cuh"
 
 #include "alloc.h"
 
@@ -711,11 +712,70 @@ __global__ void k_lincomb(int64_t dim, const double* __restrict__ X, int64_t ldx
   }
 }
 
+// The same combination in double-float arithmetic on the FP32 pipe, which issues 64 times as
+// many operations per clock as the FP64 pipe on this chip (k_lincomb is FP64-bound: nq
+// multiply-adds per loaded element).  Each X element is cut into two floats from its bits
+// (double_to_float2), each coefficient into two floats once per block; a term c x is
+// ch xh (its rounding error recovered exactly by an FMA) plus ch xl + cl xh, and the sum is
+// carried as an unevaluated float pair (two-sum with explicit round-to-nearest operations, so
+// that no multiply-add is contracted into it).  Accuracy about 2^-44 of sum_p |c_pq X_p[k]|,
+// against 2^-53 for FP64: FP64-grade for the Davidson, DIIS and GMRES combinations that use it.
+__global__ void __launch_bounds__(256) k_lincomb_df(int64_t dim, const double* __restrict__ X, int64_t ldx, int np,
+                                                    const double* __restrict__ c, int ldc, double* __restrict__ Y,
+                                                    int64_t ldy, int nq, bool accumulate) {
+  extern __shared__ float2 cs[];  // [np][nq]: (high, low) floats of each coefficient
+  for (int i = threadIdx.x; i < np * nq; i += blockDim.x) {
+    const int p = i / nq, q = i % nq;
+    const double v = c[p * ldc + q];
+    const float h = __double2float_rn(v);
+    cs[i] = make_float2(h, __double2float_rn(v - (double)h));
+  }
+  __syncthreads();
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < dim; k += (int64_t)gridDim.x * blockDim.x) {
+    for (int q0 = 0; q0 < nq; q0 += 8) {
+      float sh[8], sl[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) sh[q] = sl[q] = 0.0f;
+#pragma unroll 4
+      for (int p = 0; p < np; ++p) {
+        float xh, xl;
+        double_to_float2(X[(int64_t)p * ldx + k], xh, xl);
+        const float2* cp = cs + p * nq + q0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (q0 + q < nq) {
+            const float2 cc = cp[q];
+            const float ph = __fmul_rn(cc.x, xh);
+            const float pe = __fmaf_rn(cc.x, xh, -ph);  // ch xh - ph, exact
+            const float lo = __fmaf_rn(cc.x, xl, __fmaf_rn(cc.y, xh, pe));
+            const float t = __fadd_rn(sh[q], ph);
+            const float bp = __fsub_rn(t, sh[q]);
+            const float err = __fadd_rn(__fsub_rn(sh[q], __fsub_rn(t, bp)), __fsub_rn(ph, bp));
+            sh[q] = t;
+            sl[q] = __fadd_rn(sl[q], __fadd_rn(err, lo));
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (q0 + q >= nq) break;
+        const double v = (double)sh[q] + (double)sl[q];
+        double* y = Y + (int64_t)(q0 + q) * ldy + k;
+        *y = accumulate ? (*y + v) : v;
+      }
+    }
+  }
+}
+
 void launch_lincomb(const VecShape& s, const double* X, int64_t ldx, int np, const double* c, int ldc, double* Y,
                     int64_t ldy, int nq, bool accumulate, cudaStream_t st) {
   count_launches(1);
   int64_t dim = s.dim();
-  k_lincomb<<<grid_for(dim), 256, 0, st>>>(dim, X, ldx, np, c, ldc, Y, ldy, nq, accumulate);
+  const size_t smem = (size_t)np * nq * sizeof(float2);
+  if (smem <= 32 * 1024)
+    k_lincomb_df<<<grid_for(dim), 256, smem, st>>>(dim, X, ldx, np, c, ldc, Y, ldy, nq, accumulate);
+  else
+    k_lincomb<<<grid_for(dim), 256, 0, st>>>(dim, X, ldx, np, c, ldc, Y, ldy, nq, accumulate);
 }
 
 __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
