@@ -497,8 +497,9 @@ class Davidson {
     complex_run_ = cplx ? complex_run_ + 1 : 0;
     if (complex_run_ > 12) throw Err(CCSD_ERR_COMPLEX_ROOT, "complex eigenvalue among the wanted roots");
     const double* U = Sout.p + 2 * nroots;
-    launch_lincomb(c->vs, V.p, dim, m, U, nroots, X.p, dim, nroots, false, c->st);
-    launch_lincomb(c->vs, AV.p, dim, m, U, nroots, AX.p, dim, nroots, false, c->st);
+    // Ritz vectors in double-float arithmetic (FP64-grade, off the FP64 pipe)
+    launch_lincomb(c->vs, V.p, dim, m, U, nroots, X.p, dim, nroots, false, c->st, true);
+    launch_lincomb(c->vs, AV.p, dim, m, U, nroots, AX.p, dim, nroots, false, c->st, true);
     // residuals r_k = A x_k - omega_k x_k (x_k has unit norm up to roundoff)
     std::vector<double> xn = gram(c, X.p, dim, nroots, X.p, dim, nroots);
     std::vector<int> todo;

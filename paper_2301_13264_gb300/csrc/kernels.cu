@@ -719,7 +719,10 @@ __global__ void k_lincomb(int64_t dim, const double* __restrict__ X, int64_t ldx
 // ch xh (its rounding error recovered exactly by an FMA) plus ch xl + cl xh, and the sum is
 // carried as an unevaluated float pair (two-sum with explicit round-to-nearest operations, so
 // that no multiply-add is contracted into it).  Accuracy about 2^-44 of sum_p |c_pq X_p[k]|,
-// against 2^-53 for FP64: FP64-grade for the Davidson, DIIS and GMRES combinations that use it.
+// against 2^-53 for FP64.  Used for the Ritz vectors of the Davidson solver (fp64grade): their
+// coefficients are eigenvector components of an orthonormal basis, so the error stays 2^-44 of
+// the vector.  Combinations whose coefficients can cancel strongly (DIIS extrapolation, GMRES
+// updates, orthogonalisation of a nearly dependent vector) keep k_lincomb.
 __global__ void __launch_bounds__(256) k_lincomb_df(int64_t dim, const double* __restrict__ X, int64_t ldx, int np,
                                                     const double* __restrict__ c, int ldc, double* __restrict__ Y,
                                                     int64_t ldy, int nq, bool accumulate) {
@@ -768,11 +771,11 @@ __global__ void __launch_bounds__(256) k_lincomb_df(int64_t dim, const double* _
 }
 
 void launch_lincomb(const VecShape& s, const double* X, int64_t ldx, int np, const double* c, int ldc, double* Y,
-                    int64_t ldy, int nq, bool accumulate, cudaStream_t st) {
+                    int64_t ldy, int nq, bool accumulate, cudaStream_t st, bool fp64grade) {
   count_launches(1);
   int64_t dim = s.dim();
   const size_t smem = (size_t)np * nq * sizeof(float2);
-  if (smem <= 32 * 1024)
+  if (fp64grade && smem <= 32 * 1024)
     k_lincomb_df<<<grid_for(dim), 256, smem, st>>>(dim, X, ldx, np, c, ldc, Y, ldy, nq, accumulate);
   else
     k_lincomb<<<grid_for(dim), 256, 0, st>>>(dim, X, ldx, np, c, ldc, Y, ldy, nq, accumulate);

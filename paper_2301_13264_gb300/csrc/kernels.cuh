@@ -62,9 +62,11 @@ struct VecShape {
 int64_t wdot_work_size(int np, int nq);
 void launch_wdot(const VecShape& s, const double* X, int64_t ldx, int np, const double* Y, int64_t ldy, int nq,
                  double* G, int ldg, double* work, cudaStream_t st);
-// y_q = sum_p c[p*ldc + q] x_p (+ y_q if accumulate), q < nq.  c is a device array.
+// y_q = sum_p c[p*ldc + q] x_p (+ y_q if accumulate), q < nq.  c is a device array.  FP64, or
+// with fp64grade in double-float arithmetic on the FP32 pipe (about 2^-44 of sum_p |c x_p|; for
+// coefficients that do not cancel strongly, such as Ritz-vector components).
 void launch_lincomb(const VecShape& s, const double* X, int64_t ldx, int np, const double* c, int ldc, double* Y,
-                    int64_t ldy, int nq, bool accumulate, cudaStream_t st);
+                    int64_t ldy, int nq, bool accumulate, cudaStream_t st, bool fp64grade = false);
 // y = a*x + b*y over n elements.
 void launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st);
 // y = x / (D - shift) with D_ai = e_a - e_i, D_aibj = e_a + e_b - e_i - e_j.
