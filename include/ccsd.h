@@ -363,8 +363,7 @@ ccsd_status ccsd_inject_stall(ccsd_handle h);
  * library's device image (one per GPU that loads the library, kept until the
  * process exits).  Its device address is looked up on the first call made for
  * each device, with the handle's device made current for the call (the
- * caller's current device is restored on return): make that first call before
- * any CUDA stream capture.  All calls share the array, so calls whose GPU work
+ * caller's current device is restored on return).  All calls share the array, so calls whose GPU work
  * overlaps (different streams or threads) race and may return wrong values;
  * serialise them.  Launches 4 * ndir + 1 kernels on the handle's stream and
  * synchronises that stream before returning. */
