@@ -264,7 +264,13 @@ void Executor::exec_contract(const Op& op) {
 
   // tensor-core path: operands are gathered straight from their strided FP64
   // layout into bf16 slices (no FP64 staging copy)
-  if ((prec_ == PREC_MIXED || prec_ == PREC_FP64_TC) && flops >= tc_min_flops && Bt == 1) {
+  // tensor cores: large enough, and not mostly padding (the MMA tile pads the longer side to
+  // 128 rows, the shorter to 64 and K to 64: a rank-1 update or a dot product of two huge vectors
+  // would issue hundreds of times its work and slice operands of tens of GB)
+  auto pad = [](int64_t x, int64_t q) { return (x + q - 1) / q * q; };
+  const double padded = (double)pad(std::max(M, N), 128) * (double)pad(std::min(M, N), 64) * (double)pad(K, 64);
+  const bool tc_shape = padded <= 16.0 * (double)M * (double)N * (double)K;
+  if ((prec_ == PREC_MIXED || prec_ == PREC_FP64_TC) && flops >= tc_min_flops && Bt == 1 && tc_shape) {
     auto gather = [&](std::map<char, std::pair<int64_t, int64_t>>& es, const std::vector<char>& rows) {
       Strided g;
       std::vector<char> order = rows;
