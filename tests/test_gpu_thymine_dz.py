@@ -83,3 +83,43 @@ def test_thymine_dz_fp64_ground_state_matches_oracle(golden):
     finally:
         B.ccsd_destroy(h)
     assert abs(e - golden["e_ccsd"]) < 1e-8
+
+
+def test_thymine_dz_eigenpairs_against_the_oracle_jacobian():
+    """The refined mixed form's two lowest roots, checked with the oracle's own Jacobian at the
+    library's converged amplitudes: |A R_k - omega_k R_k| and |L_k^T A - omega_k L_k^T| are at
+    the EOM threshold (1e-9) relative to the vectors (bound 1e-8 for the plain 2-norm against
+    the solver's metric)."""
+    from oracle import ccsd as cc
+    from oracle.solvers import System, Vec
+
+    H = workload("thymine_dz")
+    o, v = H.o, H.v
+    h = B.ccsd_create(H.eps, H.h, H.B, o, v, H.naux,
+                      B.ccsd_default_options(**TOL, precision=B.PREC_MIXED, splits=3))
+    try:
+        B.ccsd_solve_ground(h)
+        w, _ = B.eom_solve_right(h, 2)
+        wl, _ = B.eom_solve_left(h, 2)
+        dim = o * v + o * o * v * v
+        t = np.zeros(dim)
+        B.ccsd_get_amplitudes(h, t)
+        R, L = np.zeros((2, dim)), np.zeros((2, dim))
+        B.ccsd_get_states(h, 2, R, L)
+    finally:
+        B.ccsd_destroy(h)
+    S = System(H.eps, H.h, H.B, o, vvvv_batch=16)
+
+    def vec(x):
+        return Vec(cc.as_t(x[:o * v].reshape(o, v)), cc.as_t(x[o * v:].reshape(o, o, v, v)))
+
+    def flat(x):
+        return np.concatenate([x.x1.numpy().reshape(-1), x.x2.numpy().reshape(-1)])
+
+    tv = vec(t)
+    for k in range(2):
+        ar = flat(S.right(tv, vec(R[k])))
+        la = flat(S.left(tv, vec(L[k])))
+        assert np.linalg.norm(ar - w[k] * R[k]) < 1e-8 * np.linalg.norm(R[k]), k
+        assert np.linalg.norm(la - wl[k] * L[k]) < 1e-8 * np.linalg.norm(L[k]), k
+    assert abs(w[0] - wl[0]) < 1e-9 and abs(w[1] - wl[1]) < 1e-9
