@@ -31,7 +31,7 @@ FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
 # DRAM bytes (read + write) of one ladder contraction (its + and - GEMM launches) from an
 # ncu capture of the current kernel (profiles/k_tc_gemm_ladder_thymine_adz.md), keyed by
 # (workload, nvec, products); a missing entry reports null (retaken whenever the kernel changes)
-LADDER_TRAFFIC = {("thymine_adz", 8, 6): (57.84 + 0.944 + 65.10 + 0.944) * 1e9}
+LADDER_TRAFFIC = {("thymine_adz", 8, 6): (54.516 + 0.948 + 50.029 + 0.944) * 1e9}
 UNIT = "transforms/s"
 
 
