@@ -20,7 +20,11 @@ from paper_2301_13264_gb300.synth import workload
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "thymine_dz.json")
-TOL = dict(tol_res=1e-10, tol_eom=1e-9, tol_lin=1e-10, max_iter=200, davidson_max_sub=96)
+# The roots are converged ten times below the stored ones' 1e-9: a root refined on its own keeps a
+# component along a neighbouring root of about |r| / (omega_l - omega_k), which a coupling of the
+# two carries at first order, while the oracle's Rayleigh-Ritz step over all four roots removes it.
+TOL = dict(tol_res=1e-10, tol_eom=1e-10, tol_lin=1e-10, max_iter=200, davidson_max_sub=96)
+TOL_PAIRS = dict(TOL, tol_eom=1e-9)  # the eigenpair check below needs the residual only
 
 
 @pytest.fixture(scope="module")
@@ -105,7 +109,7 @@ def test_thymine_dz_eigenpairs_against_the_oracle_jacobian():
     H = workload("thymine_dz")
     o, v = H.o, H.v
     h = B.ccsd_create(H.eps, H.h, H.B, o, v, H.naux,
-                      B.ccsd_default_options(**TOL, precision=B.PREC_MIXED, splits=3))
+                      B.ccsd_default_options(**TOL_PAIRS, precision=B.PREC_MIXED, splits=3))
     try:
         B.ccsd_solve_ground(h)
         w, _ = B.eom_solve_right(h, 2)
