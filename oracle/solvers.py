@@ -282,6 +282,8 @@ class System:
         2-D invariant subspace of the pair), and the solve fails only when a
         complex pair stays among the wanted roots for more than `max_complex`
         consecutive expansions.  A complex wanted root never counts as converged.
+        When the subspace would exceed maxsub it restarts from the current and the
+        previous Ritz vectors (their images carried along, no transforms).
         """
         o, v = self.o, self.v
         maxsub = maxsub or max(8 * nroots, 24)
@@ -307,6 +309,22 @@ class System:
             AV.append(apply(x))
             return True
 
+        def add_known(x, ax):
+            # as add, for a vector whose image ax = A x is known: the same combination applied to
+            # ax gives the image of the orthonormalised vector, without another transform
+            n0 = x.norm()
+            x, ax = x / n0, ax / n0
+            for _ in range(2):
+                for b, ab in zip(V, AV):
+                    c = b.dot(x)
+                    x, ax = x - b * c, ax - ab * c
+            nrm = x.norm()
+            if nrm < 1e-8:
+                return False
+            V.append(x / nrm)
+            AV.append(ax / nrm)
+            return True
+
         def combine(basis, u):
             x = basis[0] * u[0]
             for a in range(1, len(basis)):
@@ -316,6 +334,7 @@ class System:
         for g in guesses:
             add(g)
         n_complex = 0
+        prev = []  # the previous iteration's Ritz vectors and their images
         for it in range(1, maxit + 1):
             m = len(V)
             G = np.array([[V[a].dot(AV[b]) for b in range(m)] for a in range(m)])
@@ -325,7 +344,7 @@ class System:
             n_complex = n_complex + 1 if is_complex.any() else 0
             if n_complex > max_complex:
                 raise RuntimeError("complex root among the wanted roots")
-            X, res, ok = [], [], not is_complex.any()
+            X, AX, res, ok = [], [], [], not is_complex.any()
             for k in order:
                 wr, wi = w[k].real, w[k].imag
                 ur, ui = U[:, k].real, U[:, k].imag
@@ -333,6 +352,7 @@ class System:
                 if abs(wi) <= 1e-8:
                     r = axr - xr * wr
                     X.append(xr)
+                    AX.append(axr)
                     res.append((r, wr))
                     if r.norm() > tol:
                         ok = False
@@ -340,15 +360,20 @@ class System:
                 # complex Ritz pair: A(xr + i xi) - (wr + i wi)(xr + i xi), real and imaginary parts
                 xi, axi = combine(V, ui), combine(AV, ui)
                 X.extend([xr, xi])
+                AX.extend([axr, axi])
                 res.append((axr - xr * wr + xi * wi, wr))
                 res.append((axi - xi * wr - xr * wi, wr))
             if ok:
                 return np.array([w[k].real for k in order]), X, it
             if m + len(res) > maxsub:
+                # thick restart: the Ritz vectors and those of the previous iteration (the last
+                # search directions, which a restart to the Ritz vectors alone discards and which
+                # carry the convergence of a non-symmetric matrix), with their known images
                 V.clear()
                 AV.clear()
-                for x in X:
-                    add(x)
+                for x, ax in list(zip(X, AX)) + prev:
+                    add_known(x, ax)
+            prev = list(zip(X, AX))
             for (r, wk) in res:
                 if r.norm() > tol:
                     add(self.precond(r, wk))
